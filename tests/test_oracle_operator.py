@@ -1,0 +1,364 @@
+"""Pins of the oracle's weak form (Eq. WeakFormulationConservedVariables) against what
+the paper and the mathematics fix: exact mass matrices, free-stream preservation,
+discrete conservation, SIPG symmetry, closed-form penalty and point fluxes,
+order-(k+1) convergence on manufactured and exact solutions.  Some tests plant a
+mistake in the oracle (monkeypatch, CPU only) to show that the pin catches it."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from torch.func import jvp, vmap
+
+from oracle import mms, physics as ph, rk
+from oracle.basis import basis_3d, cell_points, gauss_legendre_01, lagrange_1d
+from oracle.mesh import MAP_AFFINE, MAP_CHANNEL, MAP_SINE, BoxMesh
+from oracle.operator import WHAT_ALL, WHAT_CONV, WHAT_VISC, DGOperator
+from paper_1806_03095_gb300 import inputs
+
+TGV_PHYS = ph.Physics.from_numbers(1600.0, 0.71, 0.1)
+PI = math.pi
+
+
+def tgv_mesh(N, k, mapping=MAP_AFFINE, A=0.0):
+    return BoxMesh((N,) * 3, [-PI] * 3, [PI] * 3, (1, 1, 1), k, mapping, A)
+
+
+def make_op(mesh, phys=TGV_PHYS, nqc=None, nqv=None):
+    k = mesh.k
+    return DGOperator(mesh, phys, (3 * k) // 2 + 1 if nqc is None else nqc, k + 1 if nqv is None else nqv)
+
+
+def const_state(Nc, n3):
+    U = torch.empty((Nc, 5, n3), dtype=torch.float64)
+    for c, v in enumerate((1.1, 0.3, -0.2, 0.1, 180.0)):
+        U[:, c] = v
+    return U
+
+
+# -- point physics (Eq. CompressibleNavierStokesFluxes) --------------------------------------
+def test_conv_flux_closed_form():
+    g = 1.4
+    rho, u, p = 2.0, torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64), 3.0
+    rhoE = p / (g - 1) + 0.5 * rho * float((u * u).sum())
+    U = torch.tensor([rho, *(rho * u).tolist(), rhoE], dtype=torch.float64)
+    F = ph.conv_flux(U, g)
+    assert torch.allclose(ph.pressure(U, g), torch.tensor(p, dtype=torch.float64))
+    assert torch.allclose(F[0], rho * u)
+    assert torch.allclose(F[1:4], rho * torch.outer(u, u) + p * torch.eye(3, dtype=torch.float64))
+    assert torch.allclose(F[4], (rhoE + p) * u)
+    assert torch.allclose(ph.sound_speed(U, g), torch.tensor(math.sqrt(g * p / rho), dtype=torch.float64))
+
+
+def test_visc_flux_pure_shear_closed_form():
+    """rho = 1, u = (s y, 0, 0), uniform T: tau_xy = mu s, energy flux (tau.u)_y = mu s^2 y, no heat flux."""
+    phys = TGV_PHYS
+    s, y = 0.7, 0.3
+    u = torch.tensor([s * y, 0.0, 0.0], dtype=torch.float64)
+    T = 2.0
+    rhoE = phys.c_v * T + 0.5 * float((u * u).sum())
+    U = torch.tensor([1.0, s * y, 0.0, 0.0, rhoE], dtype=torch.float64)
+    G = torch.zeros((5, 3), dtype=torch.float64)
+    G[1, 1] = s                      # d(rho u)/dy
+    G[4, 1] = s * y * s              # d(rho E)/dy = u . du/dy
+    F = ph.visc_flux(U, G, phys)
+    expect = torch.zeros((5, 3), dtype=torch.float64)
+    expect[1, 1] = expect[2, 0] = phys.mu * s
+    expect[4, 1] = phys.mu * s * s * y
+    assert torch.allclose(F, expect, atol=1e-15, rtol=1e-13)
+
+
+def test_visc_flux_heat_conduction_closed_form():
+    """Fluid at rest with grad T = (a, 0, 0) at constant rho: F_v = (0, 0, 0, 0, lambda grad T)."""
+    phys = TGV_PHYS
+    a, T = 0.4, 3.0
+    U = torch.tensor([1.5, 0.0, 0.0, 0.0, 1.5 * phys.c_v * T], dtype=torch.float64)
+    G = torch.zeros((5, 3), dtype=torch.float64)
+    G[4, 0] = 1.5 * phys.c_v * a
+    F = ph.visc_flux(U, G, phys)
+    expect = torch.zeros((5, 3), dtype=torch.float64)
+    expect[4, 0] = phys.lam * a
+    assert torch.allclose(F, expect, atol=1e-15, rtol=1e-13)
+
+
+def test_divergence_free_stress_trace():
+    """tau is trace-free (zero bulk viscosity) for any velocity gradient."""
+    phys = TGV_PHYS
+    U = torch.tensor([1.2, 0.3, -0.1, 0.2, 200.0], dtype=torch.float64)
+    G = inputs.uniform((5, 3), 3)
+    F = ph.visc_flux(U, G, phys)
+    assert abs(float(F[1, 0] + F[2, 1] + F[3, 2])) < 1e-15
+    assert torch.allclose(F[1:4], F[1:4].T)
+
+
+# -- mass matrix (Sec. 2.2.3, Sec. 2.3) -------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_affine_mass_matrix_is_kron_of_1d(k):
+    mesh = BoxMesh((2, 1, 1), [0, 0, 0], [2.0, 0.5, 0.25], (1, 1, 1), k)
+    op = make_op(mesh)
+    M = op.mass_matrices(torch.arange(1))[0].numpy()
+    x, w = gauss_legendre_01(20)
+    V, _ = lagrange_1d(mesh.nodes_1d, x)
+    M1 = (V * w[:, None]).T @ V
+    h = mesh.h
+    Mref = np.kron(M1, np.kron(M1, M1)) * h[0] * h[1] * h[2]
+    assert np.allclose(M, Mref, rtol=1e-13, atol=1e-16)
+
+
+def test_mass_solve_inverts_mass_apply_deformed():
+    mesh = tgv_mesh(2, 3, MAP_SINE, 0.05)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 5)
+    assert torch.allclose(op.mass_solve(op.mass_apply(U)), U, rtol=1e-12, atol=0)
+
+
+# -- free stream (constant U gives F(U) = 0) -----------------------------------------------------
+@pytest.mark.parametrize("mapping,A", [(MAP_AFFINE, 0.0), (MAP_SINE, 0.08)])
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_free_stream_preservation(mapping, A, k):
+    mesh = tgv_mesh(2, k, mapping, A)
+    op = make_op(mesh)
+    R = op.residual(const_state(mesh.Nc, mesh.n ** 3))
+    assert float(R.abs().max()) < 5e-12
+
+
+def test_free_stream_negative_control_underintegrated():
+    """With nq = k+1 the deformed-mesh metric terms (degree 3k-1) are under-integrated: F(U0) != 0."""
+    mesh = tgv_mesh(2, 3, MAP_SINE, 0.08)
+    op = make_op(mesh, nqc=4)
+    assert float(op.residual(const_state(mesh.Nc, mesh.n ** 3)).abs().max()) > 1e-3
+
+
+def test_free_stream_channel_mesh():
+    mesh = BoxMesh((2, 3, 2), [0, -1, 0], [2 * PI, 1, PI], (1, 0, 1), 3, MAP_CHANNEL, 1.8)
+    phys = ph.Physics.from_numbers(180.0, 0.71, 0.1, u_mach=18.3)
+    op = make_op(mesh, phys)
+    U = const_state(mesh.Nc, mesh.n ** 3)
+    U[:, 1:4] = 0.0       # at rest: the wall state mirrors to itself only for u = 0 ...
+    U[:, 4] = 1.1 * phys.c_v * phys.T_wall  # ... and T = T_wall
+    R = op.residual(U)
+    assert float(R.abs().max()) < 1e-13 * float(U.abs().max())
+
+
+# -- conservation (V = 1 lies in the test space) ------------------------------------------------
+@pytest.mark.parametrize("mapping,A", [(MAP_AFFINE, 0.0), (MAP_SINE, 0.08)])
+def test_discrete_conservation_periodic(mapping, A):
+    mesh = tgv_mesh(3, 3, mapping, A)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 11)
+    R = op.residual(U)
+    tot = R.sum((0, 2))
+    scale = R.abs().sum((0, 2))
+    assert torch.all(tot.abs() <= 1e-13 * scale)
+
+
+def test_channel_wall_conserves_mass():
+    mesh = BoxMesh((2, 2, 2), [0, -1, 0], [2 * PI, 1, PI], (1, 0, 1), 3, MAP_CHANNEL, 1.8)
+    phys = ph.Physics.from_numbers(180.0, 0.71, 0.1, u_mach=18.3, body_force=(1.0, 0.0, 0.0))
+    op = make_op(mesh, phys)
+    U = inputs.channel_state(torch.as_tensor(mesh.xyz), 1806)
+    R = op.residual(U)
+    assert abs(float(R[:, 0].sum())) <= 1e-13 * float(R[:, 0].abs().sum())
+    # body force: sum_i (V_i, F_rhs) = int F_rhs, i.e. f1 * volume for the x-momentum row
+    Fr = op.body_force(U)
+    assert abs(float(Fr[:, 1].sum()) - mesh.volume()) < 1e-11 * mesh.volume()
+
+
+def test_conservation_negative_control_one_sided_lambda(monkeypatch):
+    """Planted mistake: LLF wave speed from the own side only -> face fluxes no longer single-valued."""
+    mesh = tgv_mesh(2, 2)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 12)
+    monkeypatch.setattr(torch, "maximum", lambda a, b: a)
+    R = op.residual(U, WHAT_CONV)
+    monkeypatch.undo()
+    assert float(R[:, 0].sum().abs()) > 1e-8 * float(R[:, 0].abs().sum())
+
+
+# -- SIPG symmetry of the viscous bilinear form -------------------------------------------------
+def _linearised_visc(op, U0, W):
+    return jvp(lambda V: op.residual(V, WHAT_VISC), (U0,), (W,))[1]
+
+
+def _momentum_only(shape, seed):
+    W = inputs.uniform(shape, seed)
+    W[:, 0] = 0.0
+    W[:, 4] = 0.0
+    return W
+
+
+@pytest.mark.parametrize("mapping,A", [(MAP_AFFINE, 0.0), (MAP_SINE, 0.06)])
+def test_sipg_momentum_block_symmetric(mapping, A):
+    """At rest (u = 0) the momentum block of the linearised viscous operator is the SIPG
+    discretisation of the Lame operator, which is symmetric: <V, A W> = <W, A V>."""
+    mesh = tgv_mesh(2, 2, mapping, A)
+    op = make_op(mesh)
+    U0 = const_state(mesh.Nc, mesh.n ** 3)
+    U0[:, 1:4] = 0.0
+    V = _momentum_only(U0.shape, 1)
+    W = _momentum_only(U0.shape, 2)
+    a_vw = float((V * _linearised_visc(op, U0, W)).sum())
+    a_wv = float((W * _linearised_visc(op, U0, V)).sum())
+    assert abs(a_vw - a_wv) <= 1e-12 * abs(a_vw)
+
+
+def test_sipg_symmetry_negative_control_dropped_half_term(monkeypatch):
+    """Planted mistake: drop the -1/2 (grad V, F_v(U, [[U]])) face term -> form is no longer symmetric."""
+    mesh = tgv_mesh(2, 2)
+    op = make_op(mesh)
+    face_grads = [op.face_tables(op.nq_visc, d, s)[1] for d in range(3) for s in range(2)]
+    orig = DGOperator.test_grad
+
+    def patched(grad, Jinv, F, wdet):
+        out = orig(grad, Jinv, F, wdet)
+        return out * 0.0 if any(grad is g for g in face_grads) else out
+
+    monkeypatch.setattr(DGOperator, "test_grad", staticmethod(patched))
+    U0 = const_state(mesh.Nc, mesh.n ** 3)
+    U0[:, 1:4] = 0.0
+    V = _momentum_only(U0.shape, 1)
+    W = _momentum_only(U0.shape, 2)
+    a_vw = float((V * _linearised_visc(op, U0, W)).sum())
+    a_wv = float((W * _linearised_visc(op, U0, V)).sum())
+    assert abs(a_vw - a_wv) > 1e-6 * abs(a_vw)
+
+
+# -- penalty (Eq. TauIP_Element) -----------------------------------------------------------------
+def test_tau_ip_affine_cube():
+    mesh = tgv_mesh(4, 3)
+    op = make_op(mesh)
+    h = 2 * PI / 4
+    assert torch.allclose(op.tau_cell, torch.full_like(op.tau_cell, 3 * TGV_PHYS.nu * 16 / h), rtol=1e-13)
+
+
+def test_tau_ip_channel_wall_cells():
+    mesh = BoxMesh((2, 4, 2), [0, -1, 0], [2 * PI, 1, PI], (1, 0, 1), 3, MAP_CHANNEL, 1.8)
+    phys = ph.Physics.from_numbers(180.0, 0.71, 0.1, u_mach=18.3)
+    op = make_op(mesh, phys)
+    hx, hz = PI, PI / 2
+    yedges = np.tanh(1.8 * (2 * np.linspace(0, 1, 5) - 1)) / np.tanh(1.8)
+    cc = mesh.cell_coords()
+    for e in range(mesh.Nc):
+        cy = cc[e, 1]
+        dy = yedges[cy + 1] - yedges[cy]
+        vol = hx * hz * dy
+        wall = cy in (0, 3)
+        a_int = 2 * hx * dy + 2 * hz * dy + (1 if wall else 2) * hx * hz
+        a_bnd = hx * hz if wall else 0.0
+        expect = phys.nu * 16 * (0.5 * a_int + a_bnd) / vol
+        assert abs(float(op.tau_cell[e]) - expect) < 1e-12 * expect
+
+
+# -- convergence (order k+1) -----------------------------------------------------------------------
+def _l2_error(op, U, exact_fun):
+    nq = op.k + 3
+    pts, w = cell_points(nq)
+    phi, grad = basis_3d(op.mesh.nodes_1d, pts)
+    phi, grad, w = torch.as_tensor(phi), torch.as_tensor(grad), torch.as_tensor(w)
+    wdet = torch.abs(torch.linalg.det(op.jacobian(op.xyz, grad))) * w
+    xq = torch.einsum("pn,ean->epa", phi, op.xyz)
+    Uh = torch.einsum("pn,ecn->epc", phi, U)
+    return math.sqrt(float(((Uh - exact_fun(xq)) ** 2 * wdet[..., None]).sum()))
+
+
+MMS_PHYS = ph.Physics(gamma=1.4, R=1.0, mu=0.01, lam=0.01 * 3.5 / 0.71, rho0=1.0)
+
+
+def _mms_error(N, k, mapping, A, T=0.1, nsteps=10, plant=None):
+    """L2 error after integrating the steady manufactured problem; ``plant`` (a context
+    manager factory) is entered after the exact source is computed, so a planted
+    mistake changes the discrete operator only."""
+    mesh = BoxMesh((N,) * 3, [0.0] * 3, [2 * PI] * 3, (1, 1, 1), k, mapping, A)
+    op = make_op(mesh, MMS_PHYS)
+    U = mms.steady_exact(torch.as_tensor(mesh.xyz), MMS_PHYS.gamma)
+    S = op.body_force(U, mms.steady_source(MMS_PHYS))
+    dt = T / nsteps
+    import contextlib
+    with (plant() if plant is not None else contextlib.nullcontext()):
+        for i in range(nsteps):
+            U = rk.step(lambda V, t: op.mass_solve(-op.residual(V) + S), U, dt, i * dt)
+    Uf = vmap(mms.conserved(mms.steady_primitive, MMS_PHYS.gamma))
+    return _l2_error(op, U, lambda xq: Uf(xq.reshape(-1, 3)).reshape(xq.shape[:-1] + (5,)))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,mapping,A", [(2, MAP_AFFINE, 0.0), (3, MAP_SINE, 0.04)])
+def test_mms_navier_stokes_order(k, mapping, A):
+    e = [_mms_error(N, k, mapping, A) for N in (2, 4, 8)]
+    order = math.log2(e[1] / e[2])
+    assert order > k + 0.7, (e, order)
+
+
+def _truncation_error(N, k, mapping, A):
+    """|| L(I U_ex) + M^{-1}(V, S) ||_M for the steady manufactured field (one operator evaluation)."""
+    mesh = BoxMesh((N,) * 3, [0.0] * 3, [2 * PI] * 3, (1, 1, 1), k, mapping, A)
+    op = make_op(mesh, MMS_PHYS)
+    U = mms.steady_exact(torch.as_tensor(mesh.xyz), MMS_PHYS.gamma)
+    S = op.body_force(U, mms.steady_source(MMS_PHYS))
+    D = op.mass_solve(-op.residual(U) + S)
+    return math.sqrt(float((D * op.mass_apply(D)).sum()))
+
+
+@pytest.mark.parametrize("k,mapping,A", [(2, MAP_AFFINE, 0.0), (3, MAP_AFFINE, 0.0), (3, MAP_SINE, 0.04)])
+def test_mms_truncation_error_order_k(k, mapping, A):
+    """The DG truncation error of the interpolated manufactured solution decays like h^k."""
+    e = [_truncation_error(N, k, mapping, A) for N in (2, 4, 8)]
+    assert math.log2(e[1] / e[2]) > k - 0.4, e
+
+
+def test_mms_negative_control_energy_flux_without_pressure(monkeypatch):
+    """Planted mistake: energy flux rho E u instead of (rho E + p) u -> truncation error stalls."""
+    orig = ph.conv_flux
+    src = mms.steady_source(MMS_PHYS)  # exact source from the correct flux
+
+    def bad(U, gamma):
+        F = orig(U, gamma)
+        p = ph.pressure(U, gamma)
+        return torch.cat([F[..., :4, :], (F[..., 4, :] - p[..., None] * U[..., 1:4] / U[..., 0:1])[..., None, :]], -2)
+
+    errs = []
+    for N in (4, 8):
+        mesh = BoxMesh((N,) * 3, [0.0] * 3, [2 * PI] * 3, (1, 1, 1), 3)
+        op = make_op(mesh, MMS_PHYS)
+        U = mms.steady_exact(torch.as_tensor(mesh.xyz), MMS_PHYS.gamma)
+        S = op.body_force(U, src)
+        monkeypatch.setattr(ph, "conv_flux", bad)
+        D = op.mass_solve(-op.residual(U) + S)
+        monkeypatch.undo()
+        errs.append(math.sqrt(float((D * op.mass_apply(D)).sum())))
+    assert math.log2(errs[0] / errs[1]) < 1.0, errs
+
+
+def _entropy_wave_error(N, k, T=0.05, nsteps=5):
+    phys = ph.Physics(gamma=1.4, R=1.0, mu=0.0, lam=0.0, rho0=1.0)
+    mesh = BoxMesh((N,) * 3, [0.0] * 3, [2 * PI] * 3, (1, 1, 1), k)
+    op = make_op(mesh, phys)
+    U = mms.entropy_wave_exact(torch.as_tensor(mesh.xyz), 0.0, phys.gamma)
+    dt = T / nsteps
+    for i in range(nsteps):
+        U = rk.step(lambda V, t: op.L(V, WHAT_CONV), U, dt, i * dt)
+
+    def exact(xq):
+        return mms.entropy_wave_exact(xq.permute(0, 2, 1), T, phys.gamma).permute(0, 2, 1)
+
+    return _l2_error(op, U, exact)
+
+
+def test_euler_entropy_wave_order():
+    e = [_entropy_wave_error(N, 2) for N in (2, 4, 8)]
+    assert math.log2(e[1] / e[2]) > 2.6, e
+
+
+# -- L(U) assembly -------------------------------------------------------------------------------
+def test_L_is_minus_Minv_F_without_forcing():
+    mesh = tgv_mesh(2, 2)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 4)
+    assert torch.allclose(op.mass_apply(op.L(U)), -op.residual(U), rtol=1e-11, atol=1e-11)
+
+
+def test_what_splits_add_up():
+    mesh = tgv_mesh(2, 2)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 6)
+    assert torch.allclose(op.residual(U, WHAT_CONV) + op.residual(U, WHAT_VISC), op.residual(U), rtol=1e-12, atol=1e-11)
