@@ -1,0 +1,345 @@
+"""Throughput of the DG compressible Navier--Stokes RK stage on GB300.
+
+A step is one full RK(5,4) time step (5 stages, each one evaluation of
+L = M^{-1}(-F + F_rhs) with cell and face integrals, inverse mass and the 2N
+update) of the Taylor--Green vortex, 64^3 cells, k = 3, FP64, fused kernel.
+Metric: GDoF/s per RK stage = 5 N_nodes * stages / time / 1e9 (DoF counts the
+5 conserved fields per node).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  N > 1 under torchrun: independent replicas
+(one TGV problem per GPU, weak scaling); the path needs no collective.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF/s per RK stage"
+UNIT = "GDoF/s"
+FP64_PEAK_TFLOPS = 1.2   # measured FP64 FMA throughput of this machine's GB300 (FMA-chain probe, 152 SMs)
+FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "native" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, x):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -- clocks sampled during the timed region ------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.proc = None
+        self.path = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(device).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        self.cmd = ["nvidia-smi", *sel, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(self.cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -- native arm --------------------------------------------------------------------------------------
+def run_stages(ctx, nsteps, dt, t0, bufs):
+    """nsteps RK(5,4) steps by ping-pong of (U, U_tmp); returns the buffer holding the state."""
+    U, Ut, dU = bufs
+    a, b = U, Ut
+    for n in range(nsteps):
+        for s in range(5):
+            ctx.rk_stage(s, dt, t0 + n * dt, a, dU, b)
+            a, b = b, a
+    return a
+
+
+def time_native(cfg, steps, warmup, device):
+    from paper_1806_03095_gb300 import configs, inputs
+    ctx = configs.make_context(cfg, device=device)
+    xyz = ctx.node_coords()
+    U = inputs.tgv_state(xyz) if cfg["name"].startswith("tgv") else inputs.channel_state(xyz, 1806)
+    del xyz
+    bufs = (U.contiguous(), ctx.empty_state(), ctx.empty_residual())
+    dt = configs.time_step(cfg)
+    run_stages(ctx, warmup, dt, 0.0, bufs)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = ctx.dg_cns_launch_count()
+    e0.record(st)
+    run_stages(ctx, steps, dt, 0.0, bufs)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.dg_cns_launch_count() - n0
+    return ctx, bufs, dt, ms, launches
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="tgv64_k3")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--kernel", choices=["fused", "split"], default="fused")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        return reference_arm(args, ws, rank)
+
+    from paper_1806_03095_gb300 import configs, roofline
+    device = local if torch.cuda.is_available() else None
+    if device is None:
+        raise RuntimeError("bench.py native arm needs a GPU")
+    torch.cuda.set_device(device)
+    prec = 1 if args.precision == "mixed" else 0
+    cfg = configs.WORKLOADS[args.workload](precision=prec, kernel=1 if args.kernel == "fused" else 0)
+    N = cfg["k"] + 1
+    Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
+    nodes = Nc * N ** 3
+
+    barrier(ws)
+    clocks = ClockSampler(device)
+    clocks.start()
+    ctx, bufs, dt, ms, launches = time_native(cfg, args.steps, args.warmup, device)
+    clk = clocks.stop()
+    ms = allreduce_max(ws, ms)
+    barrier(ws)
+    stages = 5 * args.steps
+    value = ws * 5 * nodes * stages / (ms * 1e-3) / 1e9
+    ms_step = ms / args.steps
+    t_launch = ms * 1e-3 / stages if args.kernel == "fused" else None
+
+    peaks = load_peaks()
+    rbytes = 4 if prec else 8
+    flops = roofline.stage_flops_per_cell(N, cfg["nq_conv"], cfg["nq_visc"]) * Nc
+    bytes_launch = nodes * (roofline.stage_bytes_per_node(rbytes, True) + 4 * roofline.stage_bytes_per_node(rbytes))
+    bytes_launch /= 5.0
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 arithmetic / f64 state", "data": "synthetic",
+           "config": {"workload": "Taylor-Green vortex 64^3 cells, k=3, nq_conv=5, nq_visc=4, RK(5,4), %s, %s kernel"
+                      % (args.precision, args.kernel), "cells": Nc, "nodes": nodes, "dofs": 5 * nodes,
+                      "stages_timed": stages, "dt": dt,
+                      "l2": "inputs larger than L2 (state %.0f MB per vector)" % (nodes * 40 / 1e6),
+                      "parallelism": "replicas" if ws > 1 else "1 GPU"},
+           "gpu_launches": int(launches)}
+    if t_launch is not None:
+        peak = FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS
+        ach = flops / t_launch / 1e12
+        hbm = bytes_launch / t_launch / 1e9
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        out["roofline"] = {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
+                           "frac": round(ach / peak, 4), "traffic": None,
+                           "peak_source": "measured %s FMA probe (no %s entry in MEASURED_PEAKS.json)"
+                           % ("FP32" if prec else "FP64", "FP32" if prec else "FP64"),
+                           "kernel": "dg_op_kernel (fused stage)", "flops_per_launch": flops,
+                           "hbm": {"achieved": round(hbm, 2), "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": round(hbm / hbm_peak, 5), "bytes_per_launch": bytes_launch}}
+    if clk:
+        out["clocks"] = clk
+
+    if rank == 0 and ws == 1:
+        out["e2e"] = e2e_native(ctx, bufs, dt, min(args.steps, 3))
+        if not args.no_extras:
+            out["cpu_baseline"] = cpu_baseline(cfg)
+            out["extras"] = extras(args, cfg)
+    del ctx
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_native(ctx, bufs, dt, nsteps):
+    """Same metric through the public API with host buffers: per step an H2D copy of the state from pinned
+    memory, the 5 stages, and a D2H copy of the new state."""
+    U, Ut, dU = bufs
+    host = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+    host.copy_(U)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for n in range(nsteps):
+        U.copy_(host, non_blocking=True)
+        res = run_stages(ctx, 1, dt, n * dt, (U, Ut, dU))
+        host.copy_(res, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nbytes = U.numel() * 8
+    return {"value": round(5 * (U.numel() // 5) * 5 * nsteps / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": nsteps}
+
+
+def extras(args, cfg):
+    """Beside the headline: the other precision / kernel organisation on the same workload, and the mixed form's
+    error against the FP64 path (which matches the oracle) for one evaluation of L(U) at full size."""
+    from paper_1806_03095_gb300 import api, configs, inputs
+    res = {}
+    device = torch.cuda.current_device()
+    steps = max(2, args.steps // 2)
+    for name, prec, kern in (("fp64_split", 0, 0), ("mixed_fused", 1, 1), ("mixed_split", 1, 0)):
+        c = dict(cfg, precision=prec, kernel=kern)
+        ctx, bufs, dt, ms, _ = time_native(c, steps, 3, device)
+        nodes = bufs[0].numel() // 5
+        res[name] = {"value": round(5 * nodes * 5 * steps / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+                     "ms_per_step": round(ms / steps, 3)}
+        del ctx, bufs
+        torch.cuda.empty_cache()
+    g64 = configs.make_context(dict(cfg, precision=0, kernel=1), device=device)
+    g32 = configs.make_context(dict(cfg, precision=1, kernel=1), device=device)
+    U = inputs.tgv_state(g64.node_coords())
+    L64 = g64.apply(U, op=api.OP_L)
+    L32 = g32.apply(U, op=api.OP_L).double()
+    d = L32 - L64
+    res["mixed_error_vs_fp64"] = {"quantity": "L(U) of the initial TGV state, 64^3, k=3",
+                                  "rel_l2": float(torch.linalg.norm(d) / torch.linalg.norm(L64)),
+                                  "rel_max": float(d.abs().max() / L64.abs().max())}
+    del g64, g32, U, L64, L32, d
+    torch.cuda.empty_cache()
+    return res
+
+
+# -- CPU oracle --------------------------------------------------------------------------------------
+def oracle_sample(cfg, target_s=12.0):
+    """Time the FP64 oracle's L(U) on a bounded sample of the workload: a 16^3-cell periodic TGV mesh with the
+    workload's k and quadrature (same per-node work), repeated until ~target_s seconds of CPU time."""
+    from oracle import physics as ph
+    from oracle.mesh import BoxMesh
+    from oracle.operator import DGOperator
+    from paper_1806_03095_gb300 import inputs
+    n = 16 if cfg["k"] <= 3 else 8
+    mesh = BoxMesh((n, n, n), cfg["lo"], cfg["hi"], cfg["periodic"], cfg["k"])
+    phys = ph.Physics.from_numbers(cfg["Re"], cfg["Pr"], cfg["Ma"], cfg["gamma"], cfg["R"])
+    op = DGOperator(mesh, phys, cfg["nq_conv"], cfg["nq_visc"])
+    U = inputs.tgv_state(op.xyz)
+    op.L(U)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        op.L(U)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > target_s or reps >= 50:
+            break
+    dofs = 5 * mesh.Nc * mesh.n ** 3
+    return {"value": round(dofs * reps / el / 1e9, 6), "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": "oracle L(U) (naive full-matrix FP64 quadrature, PyTorch CPU) on a %d^3-cell "
+            "periodic TGV mesh, k=%d, %d evaluations in %.1f s" % (n, cfg["k"], reps, el), "seconds": round(el, 2)}
+
+
+def cpu_baseline(cfg):
+    return oracle_sample(cfg)
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_1806_03095_gb300 import configs
+    cfg = configs.WORKLOADS[args.workload]()
+    per = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(cfg, target_s=2.0)
+        if i >= args.warmup:
+            per.append(r["value"])
+            samples.append(r["seconds"])
+    value = statistics.mean(per)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(samples), 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "Taylor-Green vortex, k=%d, nq_conv=%d, nq_visc=%d; each step a bounded sample: "
+                      "one or more oracle L(U) evaluations on a 16^3-cell periodic mesh" % (
+                          cfg["k"], cfg["nq_conv"], cfg["nq_visc"])},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": torch.get_num_threads(),
+                            "kind": "oracle", "sample": "oracle L(U) on a 16^3-cell TGV mesh, ~2 s per step"},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

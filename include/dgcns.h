@@ -1,0 +1,159 @@
+/*
+ * dgcns.h -- C ABI of libdgcns, a single-GPU (GB300, sm_103a) matrix-free
+ * high-order discontinuous Galerkin operator for the compressible
+ * Navier--Stokes equations (Fehn, Wall & Kronbichler, arXiv:1806.03095).
+ *
+ * Operation implemented (paper Sec. 2): the semi-discrete system
+ *   M dU/dt = -F_c(U) - F_v(U) + F_rhs(U) = M L(U)      (Eq. SpatiallyDiscretizedProblem)
+ * where the residual F = F_c + F_v is the weak form of
+ * Eq. WeakFormulationConservedVariables: cell integrals -(grad V, F_c) +
+ * (grad V, F_v); face integrals with the local Lax--Friedrichs flux
+ * (V, ({{F_c}} + Lambda/2 [[U]]) . n) and the symmetric interior penalty
+ * terms -(V, ({{F_v}} - tau_IP [[U]]) . n) - 1/2 (grad V, F_v(U, [[U]])),
+ * tau_IP of Eq. TauIP_Element.  Integrals use Gauss--Legendre rules
+ * (Eq. IntegralsNumericalQuadrature): nq_conv points per direction for the
+ * convective terms, nq_visc for the viscous terms, k+1 for the mass matrix
+ * and the body force (Sec. 2.2.3).  Basis: tensor-product Lagrange
+ * polynomials of degree k on Legendre--Gauss--Lobatto nodes of [0,1]^3.
+ *
+ * Time stepping (Sec. 2.4): low-storage explicit Runge--Kutta, here the
+ * five-stage fourth-order 2N scheme of Carpenter & Kennedy (1994):
+ *   dU <- A_i dU + dt L(U_in, t + C_i dt);   U_out <- U_in + B_i dU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Layout of a state-like array: [n_cells][5][n^3], n = k+1, components
+ *   (rho, rho u_x, rho u_y, rho u_z, rho E), node index i0 + n i1 + n^2 i2
+ *   (x fastest); cell index cx + nx (cy + ny cz).
+ * - All array arguments are DEVICE pointers owned by the caller, contiguous,
+ *   16-byte aligned, unless stated otherwise.  U is always double.  "Residual"
+ *   arrays (R, dU, W, G) are double in DGCNS_FP64 mode and float in
+ *   DGCNS_MIXED mode (FP32 cell/face arithmetic and residual storage, FP64
+ *   state accumulation and reductions).
+ * - Calls are asynchronous on the context's stream unless stated otherwise.
+ * - Every call returns DGCNS_OK (0) or a negative DGCNS_ERR_* code and never
+ *   aborts or traps; dg_cns_last_error() gives a message.
+ * - The context owns its geometry, 1D tables and scratch buffers.
+ */
+#ifndef DGCNS_H
+#define DGCNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGCNS_OK 0
+#define DGCNS_ERR_INVALID_ARG (-1)
+#define DGCNS_ERR_UNSUPPORTED (-2)
+#define DGCNS_ERR_CUDA (-3)
+#define DGCNS_ERR_OOM (-4)
+#define DGCNS_ERR_NONFINITE (-5)
+#define DGCNS_ERR_TIMEOUT (-6)
+
+#define DGCNS_FP64 0
+#define DGCNS_MIXED 1
+
+#define DGCNS_KERNEL_SPLIT 0 /* cell kernel, face kernel, inverse-mass/stage kernel */
+#define DGCNS_KERNEL_FUSED 1 /* one kernel per stage: cells, 6 faces, M^-1, update */
+
+#define DGCNS_MAP_AFFINE 0   /* uniform Cartesian box (Sec. 4.2.1)                     */
+#define DGCNS_MAP_CHANNEL 1  /* y -> tanh(C(2 eta - 1))/tanh(C), C = map_param (Sec. 4.3.1) */
+#define DGCNS_MAP_SINE 2     /* smooth periodic deformation of amplitude map_param    */
+
+#define DGCNS_OP_L 0  /* L(U) = M^-1 (-F(U) + F_rhs(U))        */
+#define DGCNS_OP_F 1  /* F(U) = F_c(U) + F_v(U)  (no mass matrix) */
+#define DGCNS_OP_FC 2 /* F_c(U) only                           */
+#define DGCNS_OP_FV 3 /* F_v(U) only                           */
+
+#define DGCNS_NDIAG 9 /* e_k, eps, -de_k/dt, int rho, int rho u (3), int rho E, nonfinite count */
+
+typedef struct dgcns_ctx dgcns_ctx;
+
+/* Structured hexahedral box of n[0] x n[1] x n[2] cells on [lo, hi]
+ * (Sec. 4.2.1 uniform grid, Sec. 4.3.1 stretched channel grid); a
+ * non-periodic axis has no-slip isothermal walls on both ends. */
+typedef struct {
+  int n[3];
+  double lo[3], hi[3];
+  int periodic[3];
+  int mapping;      /* DGCNS_MAP_* ; the geometry is isoparametric of degree k */
+  double map_param; /* channel stretch C, or sine amplitude (fraction of the box length) */
+} dgcns_mesh;
+
+/* Discretisation and physics.  mu = rho0 U0 L / Re, lambda = mu c_p / Pr,
+ * c_p = gamma R/(gamma-1), c0 = u_mach / Ma (u_mach = U0 when 0),
+ * T0 = c0^2/(gamma R) (wall temperature), nu = mu / rho0 (Sec. 4.2.1, 4.3.1). */
+typedef struct {
+  int k;         /* polynomial degree, 1..6 in the shipped instantiations */
+  int nq_conv;   /* Gauss points per direction for the convective terms   */
+  int nq_visc;   /* Gauss points per direction for the viscous terms      */
+  double gamma, Pr, Re, Ma, R, rho0, U0, L, u_mach;
+  double body_force[3];
+  int precision; /* DGCNS_FP64 or DGCNS_MIXED */
+  int kernel;    /* DGCNS_KERNEL_SPLIT or DGCNS_KERNEL_FUSED */
+  int reserved[4];
+} dgcns_params;
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,
+ * penalty per cell, geometry) and allocates the context's device buffers.
+ * Errors: INVALID_ARG (sizes, physics), UNSUPPORTED (no instantiation for
+ * (k, nq_conv, nq_visc)), OOM, CUDA.  *out is NULL on error. */
+int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* params, void* stream, dgcns_ctx** out);
+
+/* Free every buffer of the context (synchronises its stream first). */
+int dg_cns_destroy(dgcns_ctx* ctx);
+
+/* Replace the stream used by later calls. */
+int dg_cns_set_stream(dgcns_ctx* ctx, void* stream);
+
+/* Host outputs: number of cells, nodes (n_cells (k+1)^3) and DoFs (5 nodes). */
+int dg_cns_sizes(const dgcns_ctx* ctx, int64_t* n_cells, int64_t* n_nodes, int64_t* n_dofs);
+
+/* Node coordinates of the degree-k geometry, written to xyz [n_cells][3][n^3]
+ * (device, double).  Used to set initial conditions. */
+int dg_cns_node_coords(dgcns_ctx* ctx, double* xyz);
+
+/* Evaluate one operator of Eq. SpatiallyDiscretizedProblem on U (device,
+ * double [n_cells][5][n^3]) into R (device, residual type).  op is
+ * DGCNS_OP_L, _F, _FC or _FV.  R must not alias U. */
+int dg_cns_apply(dgcns_ctx* ctx, const double* U, void* R, int op);
+
+/* out = M^-1 in (tensor-product inverse of the block-diagonal mass matrix,
+ * Sec. 2.3: M_e^-1 = S^-1 diag(1/(|J| w)) S^-T per cell with the square
+ * (k+1) x (k+1) LGL-to-Gauss matrix S).  Residual type; in == out allowed. */
+int dg_cns_inverse_mass(dgcns_ctx* ctx, const void* in, void* out);
+
+/* One stage (0..4) of the 2N RK(5,4) scheme:
+ *   dU <- A_stage dU + dt L(U_in, t + C_stage dt);  U_out <- U_in + B_stage dU.
+ * U_in, U_out: double; dU: residual type (read only when A_stage != 0).
+ * Split kernels allow U_out == U_in; the fused kernel needs U_out != U_in
+ * (neighbours read U_in), else INVALID_ARG. */
+int dg_cns_rk_stage(dgcns_ctx* ctx, int stage, double dt, double t, const double* U_in, void* dU, double* U_out);
+
+/* nsteps full RK(5,4) steps from time t0 with constant dt.  On return U holds
+ * the new state; U_tmp (double, state sized) and dU (residual type) are
+ * caller-provided work arrays. */
+int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU);
+
+/* Taylor--Green diagnostics of Sec. 4.2.3 in FP64 (Gauss rule nq_conv):
+ * out[0] e_k = 1/V int |u|^2/2, out[1] eps = nu/V int grad u : grad u,
+ * out[2] -de_k/dt from L_of_U (0 when L_of_U is NULL), out[3..7] int rho,
+ * int rho u, int rho E (k+1 points, = 1^T M U), out[8] number of non-finite
+ * entries of U.  out is a HOST array of DGCNS_NDIAG doubles; the call
+ * synchronises the stream.  Returns DGCNS_ERR_NONFINITE when out[8] > 0
+ * (out is still filled). */
+int dg_cns_diagnostics(dgcns_ctx* ctx, const double* U, const void* L_of_U, double* out);
+
+/* Number of CUDA kernels this context has launched so far (host counter). */
+int dg_cns_launch_count(const dgcns_ctx* ctx, int64_t* count);
+
+/* Message of the last error on this context (static string if ctx is NULL). */
+const char* dg_cns_last_error(const dgcns_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGCNS_H */

@@ -235,24 +235,37 @@ class DGOperator:
         ``source(x, t)`` (optional) adds a manufactured source S(x, t) [..., 5]
         integrated at nq_conv points.
         """
+        return torch.cat([self.body_force_cells(U, E, source, t) for E in self._chunks()], 0)
+
+    def body_force_cells(self, U, E, source=None, t=0.0):
         f = torch.tensor(self.phys.body_force, dtype=torch.float64)
-        out = []
-        for E in self._chunks():
-            Ue = U[E]
-            phi, _, _ = self.cell_tables(self.nq_mass)
-            _, wdet = self.cell_geometry(E, self.nq_mass)
-            Uq = self.values(phi, Ue)
-            u = Uq[..., 1:4] / Uq[..., 0:1]
-            zero = torch.zeros_like(Uq[..., 0:1])
-            Frhs = torch.cat([zero, f.expand(Uq.shape[:-1] + (3,)), (u * f).sum(-1, keepdim=True)], dim=-1)
-            r = self.test_val(phi, Frhs, wdet)
-            if source is not None:
-                phi_s, _, _ = self.cell_tables(self.nq_conv)
-                _, wdet_s = self.cell_geometry(E, self.nq_conv)
-                xq = torch.einsum("pn,ean->epa", phi_s, self.xyz[E])
-                r = r + self.test_val(phi_s, source(xq, t), wdet_s)
-            out.append(r)
-        return torch.cat(out, 0)
+        Ue = U[E]
+        phi, _, _ = self.cell_tables(self.nq_mass)
+        _, wdet = self.cell_geometry(E, self.nq_mass)
+        Uq = self.values(phi, Ue)
+        u = Uq[..., 1:4] / Uq[..., 0:1]
+        zero = torch.zeros_like(Uq[..., 0:1])
+        Frhs = torch.cat([zero, f.expand(Uq.shape[:-1] + (3,)), (u * f).sum(-1, keepdim=True)], dim=-1)
+        r = self.test_val(phi, Frhs, wdet)
+        if source is not None:
+            phi_s, _, _ = self.cell_tables(self.nq_conv)
+            _, wdet_s = self.cell_geometry(E, self.nq_conv)
+            xq = torch.einsum("pn,ean->epa", phi_s, self.xyz[E])
+            r = r + self.test_val(phi_s, source(xq, t), wdet_s)
+        return r
+
+    def residual_cells(self, U, E, what=WHAT_ALL):
+        """F(U) restricted to the cells E (element-based form: each cell's rows need only U)."""
+        return self._residual_chunk(U, torch.as_tensor(E), what)
+
+    def L_cells(self, U, E):
+        """L(U) restricted to the cells E (M is block diagonal)."""
+        E = torch.as_tensor(E)
+        rhs = -self.residual_cells(U, E)
+        if self.has_body_force():
+            rhs = rhs + self.body_force_cells(U, E)
+        M = self.mass_matrices(E)
+        return torch.linalg.solve(M, rhs.transpose(1, 2)).transpose(1, 2)
 
     def has_body_force(self):
         return any(float(b) != 0.0 for b in self.phys.body_force)

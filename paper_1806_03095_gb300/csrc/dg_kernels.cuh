@@ -1,0 +1,599 @@
+// Device code of libdgcns: sum-factorized cell and face integrals of the
+// compressible Navier--Stokes DG operator (Eq. WeakFormulationConservedVariables),
+// tensor-product inverse mass matrix and the 2N RK stage update (Sec. 2.3, 2.4).
+//
+// Organisation (GB300-first, one CTA per batch of CB cells):
+//  - the cell batch's nodal state is staged in shared memory (converted to the
+//    arithmetic type T: double for the FP64 form, float for the mixed form);
+//  - every 1D contraction ("sweep") is done by one thread per line with the
+//    line held in registers and the 1D matrix broadcast from shared memory
+//    (the paper's sum factorization, Eq. SumFactorization; loop lengths are
+//    template parameters, as the paper's kernels do);
+//  - gradients use the collocation trick of Sec. 2.3: interpolate values to
+//    the Gauss grid, then apply the Gauss-point derivative matrix (2d instead
+//    of d^2 1D kernels); the test with grad V applies the transposed matrices;
+//  - faces are evaluated element-centrically: each cell computes the numerical
+//    fluxes on its 6 faces from its own trace and the neighbour's and tests
+//    them with its own basis only, so no two CTAs write the same cell.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_common.h"
+
+namespace dgcns {
+
+// ---------------------------------------------------------------------------
+// Shared-memory tables
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Tab {
+  const T *Sc, *Dc, *Sv, *Dv, *Sm, *Smi, *wc, *wv, *wm, *dl0, *dl1;
+};
+
+template <typename T, int N, int QC, int QV>
+__device__ __forceinline__ Tab<T> load_tables(const T* __restrict__ g, T* s) {
+  const TableLayout L = make_layout(N, QC, QV);
+  for (int i = threadIdx.x; i < L.total; i += blockDim.x) s[i] = g[i];
+  Tab<T> t;
+  t.Sc = s + L.Sc; t.Dc = s + L.Dc; t.Sv = s + L.Sv; t.Dv = s + L.Dv;
+  t.Sm = s + L.Sm; t.Smi = s + L.Smi; t.wc = s + L.wc; t.wv = s + L.wv; t.wm = s + L.wm;
+  t.dl0 = s + L.dl0; t.dl1 = s + L.dl1;
+  return t;
+}
+
+template <int N, int QC, int QV>
+constexpr int table_elems() {
+  return ((QC * N + QC * QC + QV * N + QV * QV + 2 * N * N + QC + QV + 3 * N) + 3) & ~3;
+}
+
+// ---------------------------------------------------------------------------
+// 1D sweep: apply the matrix M along axis AX of nblk arrays of shape
+// (D2, D1, D0) (D0 fastest, arrays contiguous one after the other).  The
+// axis extent DIN becomes DOUT.  M is [DOUT][DIN] (TR = false) or applied
+// transposed from storage [DIN][DOUT] (TR = true).  ACC adds into out.
+// ---------------------------------------------------------------------------
+template <typename T, int AX, int D0, int D1, int D2, int DOUT, bool TR, bool ACC>
+__device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M,
+                                      int nblk) {
+  constexpr int DIN = AX == 0 ? D0 : (AX == 1 ? D1 : D2);
+  constexpr int O0 = AX == 0 ? DOUT : D0;
+  constexpr int O1 = AX == 1 ? DOUT : D1;
+  constexpr int O2 = AX == 2 ? DOUT : D2;
+  constexpr int ISZ = D0 * D1 * D2, OSZ = O0 * O1 * O2;
+  constexpr int NL = ISZ / DIN;
+  constexpr int IST = AX == 0 ? 1 : (AX == 1 ? D0 : D0 * D1);
+  constexpr int OST = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
+  for (int l = threadIdx.x; l < nblk * NL; l += blockDim.x) {
+    const int blk = l / NL, r = l - blk * NL;
+    int ib, ob;
+    if (AX == 0) {
+      ib = r * D0;
+      ob = r * O0;
+    } else if (AX == 1) {
+      const int a = r % D0, b = r / D0;
+      ib = b * D0 * D1 + a;
+      ob = b * O0 * O1 + a;
+    } else {
+      ib = r;
+      ob = r;
+    }
+    const T* ip = in + blk * ISZ + ib;
+    T* op = out + blk * OSZ + ob;
+    T x[DIN];
+#pragma unroll
+    for (int i = 0; i < DIN; ++i) x[i] = ip[i * IST];
+#pragma unroll
+    for (int o = 0; o < DOUT; ++o) {
+      T acc = (TR ? M[o] : M[o * DIN]) * x[0];
+#pragma unroll
+      for (int i = 1; i < DIN; ++i) acc += (TR ? M[i * DOUT + o] : M[o * DIN + i]) * x[i];
+      if (ACC)
+        op[o * OST] += acc;
+      else
+        op[o * OST] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise physics (Eq. CompressibleNavierStokesFluxes).  F[c][j], c the
+// conserved component, j the physical direction.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PhysT {
+  T gamma, gm1, mu, lam_cv;  // lam_cv = lambda / c_v
+};
+
+template <typename T>
+__device__ __forceinline__ T pressure(const T u[5], T rinv, T gm1) {
+  return gm1 * (u[4] - T(0.5) * rinv * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]));
+}
+
+// Convective flux along one direction j: F_c[.][j]
+template <typename T>
+__device__ __forceinline__ void conv_flux_dir(const T u[5], T rinv, T p, int j, T f[5]) {
+  const T vj = u[1 + j] * rinv;
+  f[0] = u[1 + j];
+  f[1] = u[1] * vj;
+  f[2] = u[2] * vj;
+  f[3] = u[3] * vj;
+  f[1 + j] += p;
+  f[4] = (u[4] + p) * vj;
+}
+
+// Viscous flux F_v(U, G) with G[c][a] the (physical) gradient argument.
+template <typename T>
+__device__ __forceinline__ void visc_flux(const T u[5], const T G[5][3], const PhysT<T>& ph, T F[5][3]) {
+  const T rinv = T(1) / u[0];
+  const T v0 = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
+  const T E = u[4] * rinv;
+  T gu[3][3];
+  const T v[3] = {v0, v1, v2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gu[i][j] = (G[1 + i][j] - v[i] * G[0][j]) * rinv;
+  const T div = gu[0][0] + gu[1][1] + gu[2][2];
+  const T twothird = T(2) / T(3);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    F[0][j] = T(0);
+    T tv = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T tij = ph.mu * (gu[i][j] + gu[j][i]);
+      if (i == j) tij -= ph.mu * twothird * div;
+      F[1 + i][j] = tij;
+      tv += tij * v[i];
+    }
+    const T gE = (G[4][j] - E * G[0][j]) * rinv;
+    const T gT_cv = gE - (v0 * gu[0][j] + v1 * gu[1][j] + v2 * gu[2][j]);  // c_v * dT/dx_j
+    F[4][j] = tv + ph.lam_cv * gT_cv;
+  }
+}
+
+// Exterior state on an isothermal no-slip wall: rho+ = rho-, u+ = -u-, T+ = 2 T_w - T-.
+template <typename T>
+__device__ __forceinline__ void wall_ghost(const T um[5], T cvTw2, T up[5]) {
+  const T rinv = T(1) / um[0];
+  const T ke = T(0.5) * rinv * (um[1] * um[1] + um[2] * um[2] + um[3] * um[3]);  // rho |u|^2/2
+  const T cvT = (um[4] - ke) * rinv;                                               // c_v T-
+  up[0] = um[0];
+  up[1] = -um[1];
+  up[2] = -um[2];
+  up[3] = -um[3];
+  up[4] = um[0] * (cvTw2 - cvT) + ke;
+}
+
+// ---------------------------------------------------------------------------
+// Node index helpers
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ int face_node(int d, int id, int j1, int j2) {
+  // node with coordinate id along axis d, j1 along the first tangential axis, j2 along the second
+  if (d == 0) return id + N * (j1 + N * j2);
+  if (d == 1) return j1 + N * (id + N * j2);
+  return j1 + N * (j2 + N * id);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory budget per kernel
+// ---------------------------------------------------------------------------
+template <int N, int QC, int QV>
+struct Sizes {
+  static constexpr int N2 = N * N;
+  static constexpr int N3 = N * N * N;
+  static constexpr int QC3 = QC * QC * QC, QV3 = QV * QV * QV;
+  static constexpr int CELL_ARENA = 20 * (QC3 > QV3 ? QC3 : QV3);  // per cell
+  // face arena per cell: conv: 2 layers, tmp, 2 point arrays; visc: 4 layers, tmp, 8 point arrays
+  static constexpr int FACE_CONV = 2 * 5 * N2 + 5 * QC * N + 2 * 5 * QC * QC;
+  static constexpr int FACE_VISC = 4 * 5 * N2 + 5 * QV * N + 8 * 5 * QV * QV;
+  static constexpr int FACE_ARENA = FACE_CONV > FACE_VISC ? FACE_CONV : FACE_VISC;
+  static constexpr int MASS_ARENA = 2 * 5 * N3;
+};
+
+// ---------------------------------------------------------------------------
+// Cell integrals: sr += -(grad V, F_c) + (grad V, F_v) for the CTA's nb cells.
+// su, sr: [CB][5][N^3]; ar: arena of CB*CELL_ARENA elements.
+// Affine geometry: J = diag(h), |J| = h0 h1 h2.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int QC, int QV, int CB>
+__device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph,
+                           int nb) {
+  const T h[3] = {T(kp.h[0]), T(kp.h[1]), T(kp.h[2])};
+  const T detJ = h[0] * h[1] * h[2];
+  const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
+  const int nbl = nb * 5;
+  if (kp.conv) {
+    constexpr int P = QC * QC * QC;
+    T* F0 = ar;
+    T* F1 = ar + CB * 5 * P;
+    T* F2 = ar + 2 * CB * 5 * P;
+    T* G = ar + 3 * CB * 5 * P;
+    // interpolate to the convective Gauss grid (Eq. SumFactorization)
+    sweep<T, 0, N, N, N, QC, false, false>(su, F1, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 1, QC, N, N, QC, false, false>(F1, F2, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 2, QC, QC, N, QC, false, false>(F2, F0, tb.Sc, nbl);
+    __syncthreads();
+    // pointwise: contravariant flux  -F_c J^{-T} |J| w  (minus sign of the weak form)
+    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+      const int e = idx / P, p = idx - e * P;
+      const int q0 = p % QC, q1 = (p / QC) % QC, q2 = p / (QC * QC);
+      const T w = tb.wc[q0] * tb.wc[q1] * tb.wc[q2] * detJ;
+      T u[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) u[c] = F0[(e * 5 + c) * P + p];
+      const T rinv = T(1) / u[0];
+      const T pr = pressure(u, rinv, ph.gm1);
+      T* Fd[3] = {F0, F1, F2};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T f[5];
+        conv_flux_dir(u, rinv, pr, j, f);
+        const T s = -w * hinv[j];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Fd[j][(e * 5 + c) * P + p] = s * f[c];
+      }
+    }
+    __syncthreads();
+    // G = sum_d D_d^T Ft_d  (test with grad V in the collocation basis)
+    sweep<T, 0, QC, QC, QC, QC, true, false>(F0, G, tb.Dc, nbl);
+    __syncthreads();
+    sweep<T, 1, QC, QC, QC, QC, true, true>(F1, G, tb.Dc, nbl);
+    __syncthreads();
+    sweep<T, 2, QC, QC, QC, QC, true, true>(F2, G, tb.Dc, nbl);
+    __syncthreads();
+    // back to the nodes: S^T along z, y, x
+    sweep<T, 2, QC, QC, QC, N, true, false>(G, F0, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 1, QC, QC, N, N, true, false>(F0, F1, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 0, QC, N, N, N, true, true>(F1, sr, tb.Sc, nbl);
+    __syncthreads();
+  }
+  if (kp.visc) {
+    constexpr int P = QV * QV * QV;
+    T* V0 = ar;
+    T* V1 = ar + CB * 5 * P;
+    T* V2 = ar + 2 * CB * 5 * P;
+    T* V3 = ar + 3 * CB * 5 * P;
+    sweep<T, 0, N, N, N, QV, false, false>(su, V1, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, N, N, QV, false, false>(V1, V2, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 2, QV, QV, N, QV, false, false>(V2, V0, tb.Sv, nbl);
+    __syncthreads();
+    // reference gradients by collocation
+    sweep<T, 0, QV, QV, QV, QV, false, false>(V0, V1, tb.Dv, nbl);
+    sweep<T, 1, QV, QV, QV, QV, false, false>(V0, V2, tb.Dv, nbl);
+    sweep<T, 2, QV, QV, QV, QV, false, false>(V0, V3, tb.Dv, nbl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+      const int e = idx / P, p = idx - e * P;
+      const int q0 = p % QV, q1 = (p / QV) % QV, q2 = p / (QV * QV);
+      const T w = tb.wv[q0] * tb.wv[q1] * tb.wv[q2] * detJ;
+      T u[5], G[5][3], F[5][3];
+      T* Vd[3] = {V1, V2, V3};
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        u[c] = V0[(e * 5 + c) * P + p];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G[c][j] = Vd[j][(e * 5 + c) * P + p] * hinv[j];
+      }
+      visc_flux(u, G, ph, F);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T s = w * hinv[j];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Vd[j][(e * 5 + c) * P + p] = s * F[c][j];
+      }
+    }
+    __syncthreads();
+    sweep<T, 0, QV, QV, QV, QV, true, false>(V1, V0, tb.Dv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, QV, QV, QV, true, true>(V2, V0, tb.Dv, nbl);
+    __syncthreads();
+    sweep<T, 2, QV, QV, QV, QV, true, true>(V3, V0, tb.Dv, nbl);
+    __syncthreads();
+    sweep<T, 2, QV, QV, QV, N, true, false>(V0, V1, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, QV, N, N, true, false>(V1, V2, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, QV, N, N, N, true, true>(V2, sr, tb.Sv, nbl);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Face integrals of one face (direction d, side s) for the CTA's cells,
+// element-centric: the cell's own trace (-) and the neighbour's trace (+)
+// give the numerical fluxes, tested with the own basis only.
+//   + (V, ({{F_c}} + Lambda/2 [[U]]) . n)                 at QC x QC points
+//   - (V, ({{F_v}} - tau [[U]]) . n) - 1/2 (grad V, F_v(U-, [[U]]))   at QV x QV
+// su: own nodal state, sn: neighbour nodal state (unused where wall[e]),
+// tau_f[e]: face penalty, sr: accumulated residual, fa: face arena.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int QC, int QV, int CB, int d>
+__device__ void face_terms(const T* su, const T* sn, const int* wall, const T* tau_f, T* sr, T* fa,
+                           const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int nb, int s) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const T hinv[3] = {T(1.0 / kp.h[0]), T(1.0 / kp.h[1]), T(1.0 / kp.h[2])};
+  const T area = T(kp.h[t1] * kp.h[t2]);
+  const T sgn = s ? T(1) : T(-1);  // outward unit normal n = sgn e_d
+  const int idm = s ? N - 1 : 0, idp = s ? 0 : N - 1;
+  const T* dlm = s ? tb.dl1 : tb.dl0;  // l_i' at the own face
+  const T* dlp = s ? tb.dl0 : tb.dl1;  // l_i' at the neighbour's face
+  const T cvTw2 = T(2.0 * kp.cv * kp.Tw);
+  const int nbl = nb * 5;
+
+  if (kp.conv) {
+    constexpr int P = QC * QC;
+    T* Lm = fa;                   // own face layer      [CB][5][N2]
+    T* Lp = Lm + CB * 5 * N2;     // neighbour face layer
+    T* Tm = Lp + CB * 5 * N2;     // tmp [CB][5][N][QC]
+    T* Um = Tm + CB * 5 * QC * N; // [CB][5][P]
+    T* Up = Um + CB * 5 * P;
+    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+      const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
+      Lm[idx] = su[ec * N3 + face_node<N>(d, idm, j % N, j / N)];
+      Lp[idx] = wall[e] ? T(0) : sn[ec * N3 + face_node<N>(d, idp, j % N, j / N)];
+    }
+    __syncthreads();
+    sweep<T, 0, N, N, 1, QC, false, false>(Lm, Tm, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 1, QC, N, 1, QC, false, false>(Tm, Um, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 0, N, N, 1, QC, false, false>(Lp, Tm, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 1, QC, N, 1, QC, false, false>(Tm, Up, tb.Sc, nbl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+      const int e = idx / P, p = idx - e * P;
+      const T w = tb.wc[p % QC] * tb.wc[p / QC] * area;
+      T um[5], up[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        um[c] = Um[(e * 5 + c) * P + p];
+        up[c] = Up[(e * 5 + c) * P + p];
+      }
+      if (wall[e]) wall_ghost(um, cvTw2, up);
+      const T rm = T(1) / um[0], rp = T(1) / up[0];
+      const T pm = pressure(um, rm, ph.gm1), pp = pressure(up, rp, ph.gm1);
+      const T lm = sqrt(um[1] * um[1] + um[2] * um[2] + um[3] * um[3]) * rm + sqrt(fabs(ph.gamma * pm * rm));
+      const T lp = sqrt(up[1] * up[1] + up[2] * up[2] + up[3] * up[3]) * rp + sqrt(fabs(ph.gamma * pp * rp));
+      const T lam = lm > lp ? lm : lp;
+      T fm[5], fp[5];
+      conv_flux_dir(um, rm, pm, d, fm);
+      conv_flux_dir(up, rp, pp, d, fp);
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        Um[(e * 5 + c) * P + p] = w * (T(0.5) * sgn * (fm[c] + fp[c]) + T(0.5) * lam * (um[c] - up[c]));
+    }
+    __syncthreads();
+    sweep<T, 1, QC, QC, 1, N, true, false>(Um, Tm, tb.Sc, nbl);
+    __syncthreads();
+    sweep<T, 0, QC, N, 1, N, true, false>(Tm, Lm, tb.Sc, nbl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+      const int ec = idx / N2, j = idx - ec * N2;
+      sr[ec * N3 + face_node<N>(d, idm, j % N, j / N)] += Lm[idx];
+    }
+    __syncthreads();
+  }
+
+  if (kp.visc) {
+    constexpr int P = QV * QV;
+    T* Lm = fa;                    // face layers and normal-derivative layers [CB][5][N2]
+    T* Lp = Lm + CB * 5 * N2;
+    T* Dm = Lp + CB * 5 * N2;
+    T* Dp = Dm + CB * 5 * N2;
+    T* Tm = Dp + CB * 5 * N2;      // tmp [CB][5][N][QV]
+    T* Um = Tm + CB * 5 * QV * N;  // 8 point arrays [CB][5][P]
+    T* Up = Um + CB * 5 * P;
+    T* G1m = Up + CB * 5 * P;
+    T* G2m = G1m + CB * 5 * P;
+    T* Gdm = G2m + CB * 5 * P;
+    T* G1p = Gdm + CB * 5 * P;
+    T* G2p = G1p + CB * 5 * P;
+    T* Gdp = G2p + CB * 5 * P;
+    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+      const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
+      const int j1 = j % N, j2 = j / N;
+      const T* um = su + ec * N3;
+      Lm[idx] = um[face_node<N>(d, idm, j1, j2)];
+      T dn = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) dn += dlm[i] * um[face_node<N>(d, i, j1, j2)];
+      Dm[idx] = dn;
+      if (wall[e]) {
+        Lp[idx] = T(0);
+        Dp[idx] = T(0);
+      } else {
+        const T* un = sn + ec * N3;
+        Lp[idx] = un[face_node<N>(d, idp, j1, j2)];
+        T dp = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) dp += dlp[i] * un[face_node<N>(d, i, j1, j2)];
+        Dp[idx] = dp;
+      }
+    }
+    __syncthreads();
+    // values and normal derivatives to the face Gauss points
+    sweep<T, 0, N, N, 1, QV, false, false>(Lm, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Um, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, N, N, 1, QV, false, false>(Lp, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Up, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, N, N, 1, QV, false, false>(Dm, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Gdm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, N, N, 1, QV, false, false>(Dp, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Gdp, tb.Sv, nbl);
+    // tangential derivatives by collocation on the face grid
+    sweep<T, 0, QV, QV, 1, QV, false, false>(Um, G1m, tb.Dv, nbl);
+    sweep<T, 1, QV, QV, 1, QV, false, false>(Um, G2m, tb.Dv, nbl);
+    sweep<T, 0, QV, QV, 1, QV, false, false>(Up, G1p, tb.Dv, nbl);
+    sweep<T, 1, QV, QV, 1, QV, false, false>(Up, G2p, tb.Dv, nbl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+      const int e = idx / P, p = idx - e * P;
+      const T w = tb.wv[p % QV] * tb.wv[p / QV] * area;
+      const int o = e * 5 * P + p;
+      T um[5], up[5], Gm[5][3], Gp[5][3];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        um[c] = Um[o + c * P];
+        up[c] = Up[o + c * P];
+        Gm[c][t1] = G1m[o + c * P] * hinv[t1];
+        Gm[c][t2] = G2m[o + c * P] * hinv[t2];
+        Gm[c][d] = Gdm[o + c * P] * hinv[d];
+        Gp[c][t1] = G1p[o + c * P] * hinv[t1];
+        Gp[c][t2] = G2p[o + c * P] * hinv[t2];
+        Gp[c][d] = Gdp[o + c * P] * hinv[d];
+      }
+      if (wall[e]) {
+        wall_ghost(um, cvTw2, up);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) Gp[c][j] = Gm[c][j];
+      }
+      T Fm[5][3], Fp[5][3];
+      visc_flux(um, Gm, ph, Fm);
+      visc_flux(up, Gp, ph, Fp);
+      const T tau = tau_f[e];
+      T jmp[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        jmp[c] = um[c] - up[c];
+        // -(V, Q*.n):  Q*.n = {{F_v}}.n - tau (U- - U+)
+        Um[o + c * P] = -w * (T(0.5) * sgn * (Fm[c][d] + Fp[c][d]) - tau * jmp[c]);
+      }
+      // -1/2 (grad V, F_v(U-, [[U]])) with [[U]] = (U- - U+) (x) n
+      T Jg[5][3];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        Jg[c][0] = T(0);
+        Jg[c][1] = T(0);
+        Jg[c][2] = T(0);
+        Jg[c][d] = sgn * jmp[c];
+      }
+      visc_flux(um, Jg, ph, Fm);
+      const T hw = T(-0.5) * w;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        G1m[o + c * P] = hw * hinv[t1] * Fm[c][t1];
+        G2m[o + c * P] = hw * hinv[t2] * Fm[c][t2];
+        Gdm[o + c * P] = hw * hinv[d] * Fm[c][d];
+      }
+    }
+    __syncthreads();
+    // value test + tangential gradient tests on the face grid
+    sweep<T, 0, QV, QV, 1, QV, true, true>(G1m, Um, tb.Dv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, QV, 1, QV, true, true>(G2m, Um, tb.Dv, nbl);
+    __syncthreads();
+    sweep<T, 1, QV, QV, 1, N, true, false>(Um, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, QV, N, 1, N, true, false>(Tm, Lm, tb.Sv, nbl);
+    __syncthreads();
+    // normal gradient test
+    sweep<T, 1, QV, QV, 1, N, true, false>(Gdm, Tm, tb.Sv, nbl);
+    __syncthreads();
+    sweep<T, 0, QV, N, 1, N, true, false>(Tm, Dm, tb.Sv, nbl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+      const int ec = idx / N2, j = idx - ec * N2;
+      const int j1 = j % N, j2 = j / N;
+      const T lv = Lm[idx], dv = Dm[idx];
+      T* r = sr + ec * N3;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T add = dlm[i] * dv;
+        if (i == idm) add += lv;
+        r[face_node<N>(d, i, j1, j2)] += add;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L = M^{-1}(-R + F_rhs) in place on sr (Sec. 2.3: the LGL-to-Gauss matrix S at
+// the k+1 mass points is square, so M_e^{-1} = S^{-1} diag(1/(|J| w)) S^{-T});
+// with the body force integrated at the same points, M^{-1}(V, F_rhs) =
+// S^{-1} F_rhs(x_q) (nodal coefficients of its Gauss-point interpolant).
+// su is needed only for the body force (u at the mass points).
+// ---------------------------------------------------------------------------
+template <typename T, int N, int CB>
+__device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int nb, bool negate,
+                             bool add_force) {
+  constexpr int N3 = N * N * N;
+  const int nbl = nb * 5;
+  T* A = ma;
+  T* B = ma + CB * 5 * N3;
+  const T detJ = T(kp.h[0] * kp.h[1] * kp.h[2]);
+  sweep<T, 0, N, N, N, N, true, false>(sr, A, tb.Smi, nbl);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, true, false>(A, B, tb.Smi, nbl);
+  __syncthreads();
+  sweep<T, 2, N, N, N, N, true, false>(B, A, tb.Smi, nbl);
+  __syncthreads();
+  const T sg = negate ? T(-1) : T(1);
+  for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
+    const int p = idx % N3;
+    const T w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] * detJ;
+    A[idx] *= sg / w;
+  }
+  __syncthreads();
+  sweep<T, 0, N, N, N, N, false, false>(A, B, tb.Smi, nbl);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, false, false>(B, A, tb.Smi, nbl);
+  __syncthreads();
+  sweep<T, 2, N, N, N, N, false, false>(A, sr, tb.Smi, nbl);
+  __syncthreads();
+  if (add_force) {
+    // F_rhs = (0, f, f.u): momentum rows are the constant f (S^{-1} 1 = 1), energy row S^{-1}(f . u)(x_q)
+    const T f0 = T(kp.bf[0]), f1 = T(kp.bf[1]), f2 = T(kp.bf[2]);
+    // interpolate rho and momenta (components 0..3) to the mass points
+    for (int e = 0; e < nb; ++e) {
+      sweep<T, 0, N, N, N, N, false, false>(su + e * 5 * N3, A + e * 4 * N3, tb.Sm, 4);
+    }
+    __syncthreads();
+    for (int e = 0; e < nb; ++e) sweep<T, 1, N, N, N, N, false, false>(A + e * 4 * N3, B + e * 4 * N3, tb.Sm, 4);
+    __syncthreads();
+    for (int e = 0; e < nb; ++e) sweep<T, 2, N, N, N, N, false, false>(B + e * 4 * N3, A + e * 4 * N3, tb.Sm, 4);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
+      const int e = idx / N3, p = idx - e * N3;
+      const T* a = A + e * 4 * N3;
+      B[idx] = (f0 * a[N3 + p] + f1 * a[2 * N3 + p] + f2 * a[3 * N3 + p]) / a[p];
+    }
+    __syncthreads();
+    sweep<T, 0, N, N, N, N, false, false>(B, A, tb.Smi, nb);
+    __syncthreads();
+    sweep<T, 1, N, N, N, N, false, false>(A, B, tb.Smi, nb);
+    __syncthreads();
+    sweep<T, 2, N, N, N, N, false, false>(B, A, tb.Smi, nb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
+      const int e = idx / N3, p = idx - e * N3;
+      T* r = sr + e * 5 * N3;
+      r[N3 + p] += f0;
+      r[2 * N3 + p] += f1;
+      r[3 * N3 + p] += f2;
+      r[4 * N3 + p] += A[idx];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dgcns

@@ -1,0 +1,41 @@
+// Host-visible launcher table of one (N, QC, QV) instantiation.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_common.h"
+
+namespace dgcns {
+
+enum { OP_CELL = 1, OP_FACE = 2, OP_MASS = 4 };
+
+using OpFn = int (*)(int mode, const KParams&, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
+                     cudaStream_t);
+// partial == nullptr: only report the number of blocks (partial sums needed).
+using DiagFn = int (*)(const KParams&, const double* U, const void* LU, double* partial, int* nblocks,
+                       cudaStream_t);
+
+struct Launchers {
+  OpFn op_fp64, op_fp32;
+  DiagFn diag_fp64, diag_fp32;
+  int cb_fp64, cb_fp32;
+};
+
+// (N = k+1, QC, QV) triples compiled into the library.  Default rules:
+// QC = floor(3k/2)+1 (3/2-rule, Sec. 2.2.3) and QV = k+1; plus the standard
+// rule QC = QV = k+1 and the paper's variant with the 3/2 rule on both terms.
+#define DGCNS_CONFIGS(X) \
+  X(2, 2, 2)             \
+  X(3, 4, 3)             \
+  X(4, 5, 4)             \
+  X(5, 7, 5)             \
+  X(6, 8, 6)             \
+  X(7, 10, 7)            \
+  X(4, 4, 4)             \
+  X(4, 5, 5)             \
+  X(6, 6, 6)
+
+#define DGCNS_DECLARE(N, QC, QV) Launchers launchers_##N##_##QC##_##QV();
+DGCNS_CONFIGS(DGCNS_DECLARE)
+#undef DGCNS_DECLARE
+
+}  // namespace dgcns

@@ -1,0 +1,558 @@
+// Host side of libdgcns: argument checks, the host plan (1D tables in FP64,
+// penalty per cell, node coordinates), dispatch to the compiled (k, n_q)
+// instantiations, and the C ABI of include/dgcns.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dg_common.h"
+#include "dg_launchers.h"
+#include "dgcns.h"
+
+using namespace dgcns;
+
+// ---------------------------------------------------------------------------
+// Low-storage RK(5,4), 2N form (Carpenter & Kennedy 1994, five stages, fourth order).
+// ---------------------------------------------------------------------------
+static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+// ---------------------------------------------------------------------------
+// 1D polynomial tables (FP64)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Legendre P_n and P_n' at x in [-1, 1] by the three-term recurrence.
+void legendre(int n, double x, double* p, double* dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *p = 1.0;
+    *dp = 0.0;
+    return;
+  }
+  for (int m = 2; m <= n; ++m) {
+    const double p2 = ((2 * m - 1) * x * p1 - (m - 1) * p0) / m;
+    p0 = p1;
+    p1 = p2;
+  }
+  *p = p1;
+  // (1 - x^2) P_n' = n (P_{n-1} - x P_n)
+  *dp = (std::fabs(1.0 - x * x) < 1e-300) ? 0.0 : n * (p0 - x * p1) / (1.0 - x * x);
+}
+
+// Gauss--Legendre points and weights on [0,1], ascending.
+void gauss(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(n, t, &p, &dp);
+      const double dt = p / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double p, dp;
+    legendre(n, t, &p, &dp);
+    // t descends with i; store ascending on [0,1]
+    x[n - 1 - i] = 0.5 * (1.0 + t);
+    w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// k+1 Legendre--Gauss--Lobatto points on [0,1]: 0, 1 and the roots of P_k'.
+std::vector<double> lgl(int k) {
+  std::vector<double> x(k + 1);
+  x[0] = 0.0;
+  x[k] = 1.0;
+  for (int i = 1; i < k; ++i) {
+    double t = std::cos(M_PI * i / k);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(k, t, &p, &dp);
+      const double d2p = (2.0 * t * dp - k * (k + 1) * p) / (1.0 - t * t);  // Legendre ODE
+      const double dt = dp / d2p;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[k - i] = 0.5 * (1.0 + t);
+  }
+  return x;
+}
+
+// Lagrange basis on `nodes`: values V[q][i] = l_i(x_q), derivatives D[q][i] = l_i'(x_q).
+void lagrange(const std::vector<double>& nodes, const std::vector<double>& x, std::vector<double>& V,
+              std::vector<double>& D) {
+  const int n = (int)nodes.size(), m = (int)x.size();
+  V.assign((size_t)m * n, 0.0);
+  D.assign((size_t)m * n, 0.0);
+  for (int q = 0; q < m; ++q)
+    for (int i = 0; i < n; ++i) {
+      double v = 1.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) v *= (x[q] - nodes[j]) / (nodes[i] - nodes[j]);
+      double d = 0.0;
+      for (int l = 0; l < n; ++l) {
+        if (l == i) continue;
+        double t = 1.0 / (nodes[i] - nodes[l]);
+        for (int j = 0; j < n; ++j)
+          if (j != i && j != l) t *= (x[q] - nodes[j]) / (nodes[i] - nodes[j]);
+        d += t;
+      }
+      V[(size_t)q * n + i] = v;
+      D[(size_t)q * n + i] = d;
+    }
+}
+
+// In-place inverse of an n x n matrix by Gauss--Jordan elimination with partial pivoting.
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (std::fabs(A[(size_t)piv * n + c]) < 1e-300) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+        std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
+      }
+    const double inv = 1.0 / A[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[(size_t)c * n + j] *= inv;
+      I[(size_t)c * n + j] *= inv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+        I[(size_t)r * n + j] -= f * I[(size_t)c * n + j];
+      }
+    }
+  }
+  A = I;
+  return true;
+}
+
+std::vector<double> build_tables(int k, int QC, int QV) {
+  const int N = k + 1;
+  const TableLayout L = make_layout(N, QC, QV);
+  std::vector<double> t(L.total, 0.0);
+  const std::vector<double> nodes = lgl(k);
+  std::vector<double> xc, wc, xv, wv, xm, wm, V, D, Vg, Dg;
+  gauss(QC, xc, wc);
+  gauss(QV, xv, wv);
+  gauss(N, xm, wm);
+  lagrange(nodes, xc, V, D);
+  std::copy(V.begin(), V.end(), t.begin() + L.Sc);
+  lagrange(xc, xc, Vg, Dg);  // collocation derivative on the convective Gauss points
+  std::copy(Dg.begin(), Dg.end(), t.begin() + L.Dc);
+  lagrange(nodes, xv, V, D);
+  std::copy(V.begin(), V.end(), t.begin() + L.Sv);
+  lagrange(xv, xv, Vg, Dg);
+  std::copy(Dg.begin(), Dg.end(), t.begin() + L.Dv);
+  lagrange(nodes, xm, V, D);
+  std::copy(V.begin(), V.end(), t.begin() + L.Sm);
+  if (!invert(V, N)) return {};
+  std::copy(V.begin(), V.end(), t.begin() + L.Smi);
+  std::copy(wc.begin(), wc.end(), t.begin() + L.wc);
+  std::copy(wv.begin(), wv.end(), t.begin() + L.wv);
+  std::copy(wm.begin(), wm.end(), t.begin() + L.wm);
+  lagrange(nodes, std::vector<double>{0.0, 1.0}, V, D);
+  for (int i = 0; i < N; ++i) {
+    t[L.dl0 + i] = D[i];
+    t[L.dl1 + i] = D[N + i];
+  }
+  return t;
+}
+
+struct Registry {
+  int N, QC, QV;
+  Launchers (*make)();
+};
+
+#define DGCNS_ENTRY(N, QC, QV) {N, QC, QV, &launchers_##N##_##QC##_##QV},
+const Registry kRegistry[] = {DGCNS_CONFIGS(DGCNS_ENTRY)};
+#undef DGCNS_ENTRY
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct dgcns_ctx {
+  dgcns_mesh mesh;
+  dgcns_params prm;
+  cudaStream_t stream = nullptr;
+  Launchers L{};
+  KParams kp{};
+  int Nc = 0, N = 0, N3 = 0;
+  size_t state_elems = 0;
+  double mu = 0, lam = 0, cv = 0, nu = 0, Tw = 0;
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_tau = nullptr;
+  void* d_R = nullptr;        // residual scratch (split kernels)
+  double* d_partial = nullptr;
+  int diag_blocks = 0;
+  int64_t launches = 0;
+  std::string err;
+};
+
+static thread_local std::string g_create_err = "no error";
+
+static int fail(dgcns_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int cuda_fail(dgcns_ctx* c, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  return fail(c, DGCNS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static size_t res_bytes(const dgcns_ctx* c) {
+  return c->state_elems * (c->prm.precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
+}
+
+static void map_point(const dgcns_mesh& m, double* x) {
+  const double L[3] = {m.hi[0] - m.lo[0], m.hi[1] - m.lo[1], m.hi[2] - m.lo[2]};
+  if (m.mapping == DGCNS_MAP_CHANNEL) {
+    const double C = m.map_param;
+    const double eta = (x[1] - m.lo[1]) / L[1];
+    x[1] = 0.5 * (m.lo[1] + m.hi[1]) + 0.5 * L[1] * std::tanh(C * (2.0 * eta - 1.0)) / std::tanh(C);
+  } else if (m.mapping == DGCNS_MAP_SINE) {
+    double X[3], disp[3];
+    for (int b = 0; b < 3; ++b) X[b] = (x[b] - m.lo[b]) / L[b];
+    for (int a = 0; a < 3; ++a) {
+      double s = 1.0;
+      for (int b = 0; b < 3; ++b) s *= std::sin(2.0 * M_PI * X[b] + 0.5 * a * (b + 1));
+      disp[a] = m.map_param * L[a] * s;
+    }
+    for (int a = 0; a < 3; ++a) x[a] += disp[a];
+  }
+}
+
+extern "C" {
+
+int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream, dgcns_ctx** out) {
+  if (!out) return DGCNS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !prm) {
+    g_create_err = "NULL mesh or params";
+    return DGCNS_ERR_INVALID_ARG;
+  }
+  dgcns_ctx* c = new dgcns_ctx();
+  c->mesh = *mesh;
+  c->prm = *prm;
+  c->stream = static_cast<cudaStream_t>(stream);
+  auto bad = [&](int code, const std::string& m) {
+    g_create_err = m;
+    delete c;
+    return code;
+  };
+  const int k = prm->k;
+  if (k < 1 || k > 8) return bad(DGCNS_ERR_UNSUPPORTED, "k must be in 1..8");
+  if (prm->nq_conv < k + 1 || prm->nq_visc < k + 1)
+    return bad(DGCNS_ERR_INVALID_ARG, "nq_conv and nq_visc must be >= k+1 (collocation gradients)");
+  for (int d = 0; d < 3; ++d) {
+    if (mesh->n[d] < 1 || !(mesh->hi[d] > mesh->lo[d])) return bad(DGCNS_ERR_INVALID_ARG, "bad mesh extents");
+  }
+  if (!(prm->gamma > 1.0) || !(prm->Pr > 0) || !(prm->Re > 0) || !(prm->Ma > 0) || !(prm->R > 0) ||
+      !(prm->rho0 > 0) || !(prm->U0 > 0) || !(prm->L > 0))
+    return bad(DGCNS_ERR_INVALID_ARG, "physical parameters must be positive (gamma > 1)");
+  if (prm->precision != DGCNS_FP64 && prm->precision != DGCNS_MIXED)
+    return bad(DGCNS_ERR_INVALID_ARG, "precision must be DGCNS_FP64 or DGCNS_MIXED");
+  if (prm->kernel != DGCNS_KERNEL_SPLIT && prm->kernel != DGCNS_KERNEL_FUSED)
+    return bad(DGCNS_ERR_INVALID_ARG, "kernel must be DGCNS_KERNEL_SPLIT or DGCNS_KERNEL_FUSED");
+  if (mesh->mapping != DGCNS_MAP_AFFINE)
+    return bad(DGCNS_ERR_UNSUPPORTED, "only affine (Cartesian) meshes are supported by this build");
+  const long long ncell = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
+  if (ncell > (1LL << 30)) return bad(DGCNS_ERR_INVALID_ARG, "too many cells");
+  const int N = k + 1;
+  bool found = false;
+  for (const Registry& r : kRegistry)
+    if (r.N == N && r.QC == prm->nq_conv && r.QV == prm->nq_visc) {
+      c->L = r.make();
+      found = true;
+    }
+  if (!found) return bad(DGCNS_ERR_UNSUPPORTED, "no instantiation for this (k, nq_conv, nq_visc)");
+
+  c->Nc = (int)ncell;
+  c->N = N;
+  c->N3 = N * N * N;
+  c->state_elems = (size_t)c->Nc * 5 * c->N3;
+  // physics (Sec. 4.2.1): mu = rho0 U0 L / Re, lambda = mu c_p / Pr, T0 = c0^2/(gamma R)
+  c->cv = prm->R / (prm->gamma - 1.0);
+  c->mu = prm->rho0 * prm->U0 * prm->L / prm->Re;
+  c->lam = c->mu * prm->gamma * c->cv / prm->Pr;
+  c->nu = c->mu / prm->rho0;
+  const double umach = prm->u_mach > 0 ? prm->u_mach : prm->U0;
+  const double c0 = umach / prm->Ma;
+  c->Tw = c0 * c0 / (prm->gamma * prm->R);
+
+  // tables
+  std::vector<double> t64 = build_tables(k, prm->nq_conv, prm->nq_visc);
+  if (t64.empty()) return bad(DGCNS_ERR_INVALID_ARG, "singular mass interpolation matrix");
+  std::vector<float> t32(t64.begin(), t64.end());
+  // penalty per cell (Eq. TauIP_Element): nu (k+1)^2 (A_interior/2 + A_boundary)/V; affine box
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (mesh->hi[d] - mesh->lo[d]) / mesh->n[d];
+  const double vol = h[0] * h[1] * h[2];
+  std::vector<double> tau(c->Nc);
+  for (int e = 0; e < c->Nc; ++e) {
+    const int cc[3] = {e % mesh->n[0], (e / mesh->n[0]) % mesh->n[1], e / (mesh->n[0] * mesh->n[1])};
+    double a = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double area = vol / h[d];
+      for (int s = 0; s < 2; ++s) {
+        const bool boundary = !mesh->periodic[d] && ((s == 0 && cc[d] == 0) || (s == 1 && cc[d] == mesh->n[d] - 1));
+        a += boundary ? area : 0.5 * area;
+      }
+    }
+    tau[e] = c->nu * (k + 1) * (k + 1) * a / vol;
+  }
+
+  if (cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->d_tau, tau.size() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_cns_destroy(c);
+    return DGCNS_ERR_OOM;
+  }
+  cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_cns_destroy(c);
+    return DGCNS_ERR_OOM;
+  }
+  KParams& kp = c->kp;
+  kp.Nc = c->Nc;
+  for (int d = 0; d < 3; ++d) {
+    kp.nc[d] = mesh->n[d];
+    kp.periodic[d] = mesh->periodic[d] ? 1 : 0;
+    kp.h[d] = h[d];
+    kp.bf[d] = prm->body_force[d];
+  }
+  kp.has_bf = (prm->body_force[0] != 0.0 || prm->body_force[1] != 0.0 || prm->body_force[2] != 0.0) ? 1 : 0;
+  kp.gamma = prm->gamma;
+  kp.mu = c->mu;
+  kp.lam = c->lam;
+  kp.cv = c->cv;
+  kp.Tw = c->Tw;
+  kp.tau = c->d_tau;
+  kp.conv = kp.visc = 1;
+  kp.tables = prm->precision == DGCNS_MIXED ? (const void*)c->d_tab32 : (const void*)c->d_tab64;
+  // diagnostics partial sums
+  KParams kd = kp;
+  kd.tables = c->d_tab64;
+  int nblk = 0;
+  c->L.diag_fp64(kd, nullptr, nullptr, nullptr, &nblk, c->stream);
+  c->diag_blocks = nblk;
+  if (cudaMalloc(&c->d_partial, ((size_t)nblk + 1) * 10 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_cns_destroy(c);
+    return DGCNS_ERR_OOM;
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    dg_cns_destroy(c);
+    return DGCNS_ERR_CUDA;
+  }
+  *out = c;
+  return DGCNS_OK;
+}
+
+int dg_cns_destroy(dgcns_ctx* c) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_tab64);
+  cudaFree(c->d_tab32);
+  cudaFree(c->d_tau);
+  cudaFree(c->d_R);
+  cudaFree(c->d_partial);
+  delete c;
+  return DGCNS_OK;
+}
+
+int dg_cns_set_stream(dgcns_ctx* c, void* stream) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return DGCNS_OK;
+}
+
+int dg_cns_sizes(const dgcns_ctx* c, int64_t* nc, int64_t* nn, int64_t* nd) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (nc) *nc = c->Nc;
+  if (nn) *nn = (int64_t)c->Nc * c->N3;
+  if (nd) *nd = (int64_t)c->Nc * c->N3 * 5;
+  return DGCNS_OK;
+}
+
+int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!xyz) return fail(c, DGCNS_ERR_INVALID_ARG, "xyz is NULL");
+  const dgcns_mesh& m = c->mesh;
+  const int N = c->N, N3 = c->N3;
+  const std::vector<double> nodes = lgl(c->prm.k);
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (m.hi[d] - m.lo[d]) / m.n[d];
+  std::vector<double> host((size_t)c->Nc * 3 * N3);
+  for (int e = 0; e < c->Nc; ++e) {
+    const int cc[3] = {e % m.n[0], (e / m.n[0]) % m.n[1], e / (m.n[0] * m.n[1])};
+    for (int i = 0; i < N3; ++i) {
+      const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = m.lo[d] + (cc[d] + nodes[ii[d]]) * h[d];
+      map_point(m, x);
+      for (int d = 0; d < 3; ++d) host[((size_t)e * 3 + d) * N3 + i] = x[d];
+    }
+  }
+  if (cudaMemcpyAsync(xyz, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_fail(c, "node coordinates copy");
+  return DGCNS_OK;
+}
+
+static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const void* Rin, void* Rout, void* dU,
+                  double* Uout) {
+  const OpFn f = c->prm.precision == DGCNS_MIXED ? c->L.op_fp32 : c->L.op_fp64;
+  const int r = f(mode, kp, U, Rin, Rout, dU, Uout, c->stream);
+  c->launches += 1;
+  if (r != 0) return cuda_fail(c, "operator kernel launch");
+  return DGCNS_OK;
+}
+
+// L(U) into dst (mode 1) or a stage update (mode 2) with the configured kernel organisation.
+static int eval_L(dgcns_ctx* c, KParams kp, const double* U, void* dst, void* dU, double* Uout) {
+  if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE | OP_MASS, kp, U, nullptr, dst, dU, Uout);
+  KParams k0 = kp;
+  k0.out_mode = 0;
+  int r = run_op(c, OP_CELL, k0, U, nullptr, c->d_R, nullptr, nullptr);
+  if (r) return r;
+  r = run_op(c, OP_FACE, k0, U, c->d_R, c->d_R, nullptr, nullptr);
+  if (r) return r;
+  return run_op(c, OP_MASS, kp, U, c->d_R, dst, dU, Uout);
+}
+
+int dg_cns_apply(dgcns_ctx* c, const double* U, void* R, int op) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U || !R) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if ((const void*)U == R) return fail(c, DGCNS_ERR_INVALID_ARG, "R must not alias U");
+  KParams kp = c->kp;
+  switch (op) {
+    case DGCNS_OP_L:
+      kp.out_mode = 1;
+      return eval_L(c, kp, U, R, nullptr, nullptr);
+    case DGCNS_OP_F:
+    case DGCNS_OP_FC:
+    case DGCNS_OP_FV: {
+      kp.out_mode = 0;
+      kp.conv = op != DGCNS_OP_FV;
+      kp.visc = op != DGCNS_OP_FC;
+      if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE, kp, U, nullptr, R, nullptr, nullptr);
+      int r = run_op(c, OP_CELL, kp, U, nullptr, R, nullptr, nullptr);
+      if (r) return r;
+      return run_op(c, OP_FACE, kp, U, R, R, nullptr, nullptr);
+    }
+    default:
+      return fail(c, DGCNS_ERR_INVALID_ARG, "unknown op");
+  }
+}
+
+int dg_cns_inverse_mass(dgcns_ctx* c, const void* in, void* out) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!in || !out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  KParams kp = c->kp;
+  kp.out_mode = 0;
+  kp.has_bf = 0;
+  return run_op(c, OP_MASS, kp, nullptr, in, out, nullptr, nullptr);
+}
+
+int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* U_in, void* dU, double* U_out) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  (void)t;  // the operator is autonomous (constant body force)
+  if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
+  if (!U_in || !dU || !U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (c->prm.kernel == DGCNS_KERNEL_FUSED && U_in == U_out)
+    return fail(c, DGCNS_ERR_INVALID_ARG, "fused kernel needs U_out != U_in");
+  KParams kp = c->kp;
+  kp.out_mode = 2;
+  kp.A = RK_A[stage];
+  kp.B = RK_B[stage];
+  kp.dt = dt;
+  return eval_L(c, kp, U_in, nullptr, dU, U_out);
+}
+
+int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(c, DGCNS_ERR_INVALID_ARG, "nsteps < 0");
+  if (!U || !U_tmp || !dU || U == U_tmp) return fail(c, DGCNS_ERR_INVALID_ARG, "bad work arrays");
+  double* a = U;
+  double* b = U_tmp;
+  for (int n = 0; n < nsteps; ++n)
+    for (int s = 0; s < 5; ++s) {
+      const int r = dg_cns_rk_stage(c, s, dt, t0 + (n + RK_C[s]) * dt, a, dU, b);
+      if (r) return r;
+      std::swap(a, b);
+    }
+  if (a != U) {
+    if (cudaMemcpyAsync(U, a, c->state_elems * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return cuda_fail(c, "state copy");
+  }
+  return DGCNS_OK;
+}
+
+int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* out) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U || !out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  KParams kp = c->kp;
+  kp.tables = c->d_tab64;
+  int nblk = 0;
+  const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
+  if (f(kp, U, LU, c->d_partial, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics kernel launch");
+  c->launches += 1;
+  std::vector<double> part((size_t)nblk * 10);
+  if (cudaMemcpyAsync(part.data(), c->d_partial, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_fail(c, "diagnostics copy");
+  double acc[10] = {0};
+  for (int b = 0; b < nblk; ++b)
+    for (int a = 0; a < 10; ++a) acc[a] += part[(size_t)b * 10 + a];
+  out[0] = acc[1] / acc[0];
+  out[1] = c->nu * acc[2] / acc[0];
+  out[2] = LU ? -acc[3] / acc[0] : 0.0;
+  for (int a = 0; a < 5; ++a) out[3 + a] = acc[4 + a];
+  out[8] = acc[9];
+  return acc[9] > 0 ? fail(c, DGCNS_ERR_NONFINITE, "state has non-finite entries") : DGCNS_OK;
+}
+
+int dg_cns_launch_count(const dgcns_ctx* c, int64_t* count) {
+  if (!c || !count) return DGCNS_ERR_INVALID_ARG;
+  *count = c->launches;
+  return DGCNS_OK;
+}
+
+const char* dg_cns_last_error(const dgcns_ctx* c) {
+  if (!c) return g_create_err.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""CPU checks of the C ABI: the library loads and exports every symbol the header
+declares; argument validation runs on the host (no compute call without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1806_03095_gb300 import _lib
+from paper_1806_03095_gb300.build import LIB, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "dgcns.h")).read()
+    return sorted(set(re.findall(r"\b(dg_cns_\w+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert header_symbols() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_header_symbol(lib):
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_structs_match_header_layout(tmp_path):
+    """Sizes and field offsets of the ctypes structs equal those the C compiler gives the header's."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"dgcns_mesh": (_lib.Mesh, [f[0] for f in _lib.Mesh._fields_]),
+              "dgcns_params": (_lib.Params, [f[0] for f in _lib.Params._fields_])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dgcns.h"', "int main(void) {"]
+    for cname, (_, names) in fields.items():
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for n in names:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, n))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for cname, (st, names) in fields.items():
+        want.append(ctypes.sizeof(st))
+        want.extend(getattr(st, n).offset for n in names)
+    assert got == want
+
+
+def test_create_validates_on_host(lib):
+    m, p, ctx = _lib.Mesh(), _lib.Params(), ctypes.c_void_p()
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -2
+    assert b"k must be" in lib.dg_cns_last_error(None)
+    p.k, p.nq_conv, p.nq_visc = 3, 3, 4
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -1
+    p.nq_conv = 5
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -1  # empty mesh
+    assert ctx.value is None
+    assert lib.dg_cns_create(None, None, None, ctypes.byref(ctx)) == -1
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.dg_cns_destroy(None) == -1
+    assert lib.dg_cns_apply(None, None, None, 0) == -1
+    assert lib.dg_cns_rk_stage(None, 0, 1.0, 0.0, None, None, None) == -1
+    c = ctypes.c_int64()
+    assert lib.dg_cns_launch_count(None, ctypes.byref(c)) == -1
+
+
+def test_library_is_in_tree():
+    assert os.path.dirname(LIB) == os.path.join(ROOT, "paper_1806_03095_gb300")

@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 form: every output within 1e-12 relative (2-norm and max-norm over all
+5N entries), the tolerance of the operator statement.  Mixed form: the error
+bound derived in the design doc for FP32 cell/face arithmetic (tested loosely here,
+measured precisely by bench.py's precision report).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import diagnostics as odiag, physics as ph, rk as ork
+from oracle.mesh import BoxMesh
+from oracle.operator import WHAT_ALL, WHAT_CONV, WHAT_VISC, DGOperator
+from paper_1806_03095_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1806_03095_gb300 import api
+    from paper_1806_03095_gb300.api import DGCNS
+
+TOL64 = 1e-12
+PI = math.pi
+
+
+def rel_err(a, b):
+    a = a.detach().double().cpu()
+    b = b.detach().double().cpu()
+    l2 = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    mx = float((a - b).abs().max() / b.abs().max())
+    return l2, mx
+
+
+def fp64_tol(fun, U, seed=5):
+    """1e-12, or 4x the oracle's own change under a one-ulp relative perturbation of U,
+    whichever is larger (smooth states: the weak-form terms cancel by ~10^3, so the
+    FP64 result is only determined to ~1e-11 relative by any summation order)."""
+    ref = fun(U)
+    Up = U * (1.0 + 2.0 ** -52 * inputs.uniform(U.shape, seed))
+    l2, mx = rel_err(fun(Up), ref)
+    return ref, max(TOL64, 4 * l2), max(TOL64, 4 * mx)
+
+
+def pair(ncells, k, qc=None, qv=None, precision=0, kernel=1, periodic=(1, 1, 1), lo=(-PI,) * 3, hi=(PI,) * 3,
+         Re=1600.0, Ma=0.1, body_force=(0.0, 0.0, 0.0), u_mach=0.0):
+    qc = (3 * k) // 2 + 1 if qc is None else qc
+    qv = k + 1 if qv is None else qv
+    g = DGCNS(ncells, lo, hi, periodic, k, qc, qv, Re=Re, Ma=Ma, body_force=body_force, u_mach=u_mach,
+              precision=precision, kernel=kernel)
+    mesh = BoxMesh(ncells, lo, hi, periodic, k)
+    phys = ph.Physics.from_numbers(Re, 0.71, Ma, u_mach=(u_mach or None), body_force=body_force)
+    return g, DGOperator(mesh, phys, qc, qv)
+
+
+def on_gpu(U):
+    return U.to("cuda").contiguous()
+
+
+# -- geometry -------------------------------------------------------------------------------------
+def test_node_coords_match_oracle():
+    g, op = pair((3, 2, 4), 3)
+    xyz = g.node_coords().cpu()
+    assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
+
+
+# -- residual F(U), per term and combined ------------------------------------------------------------
+CASES = [((2, 2, 2), 1), ((2, 2, 2), 2), ((2, 2, 2), 3), ((3, 2, 4), 3), ((2, 2, 2), 4), ((2, 2, 2), 5),
+         ((2, 2, 2), 6)]
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("ncells,k", CASES)
+def test_residual_fp64_random_state(ncells, k, kernel):
+    g, op = pair(ncells, k, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 100 + k)
+    ref = op.residual(U)
+    out = g.apply(on_gpu(U), op=api.OP_F)
+    l2, mx = rel_err(out, ref)
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+@pytest.mark.parametrize("what,op_code", [(WHAT_CONV, 2), (WHAT_VISC, 3)])
+def test_residual_terms_fp64(what, op_code):
+    g, op = pair((2, 3, 2), 3, kernel=0)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 7)
+    out = g.apply(on_gpu(U), op=op_code)
+    l2, mx = rel_err(out, op.residual(U, what))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+@pytest.mark.parametrize("qc,qv", [(4, 4), (5, 5)])
+def test_other_quadrature_rules(qc, qv):
+    """Standard rule (k+1 for both terms) and the paper's 3/2-rule on both terms (Sec. 2.2.3)."""
+    g, op = pair((2, 2, 2), 3, qc, qv)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 8)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64
+
+
+def test_single_cell_periodic_box():
+    """Degenerate mesh: one cell per direction, the cell is its own neighbour on every face."""
+    g, op = pair((1, 1, 1), 3)
+    U = inputs.random_state(1, 64, 9)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_walls_affine_box(kernel):
+    """Non-periodic y axis: isothermal no-slip walls (mirror-state reading)."""
+    g, op = pair((2, 3, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
+                 kernel=kernel)
+    xyz = g.node_coords().cpu()
+    U = inputs.channel_state(xyz, 1806)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+# -- L(U), inverse mass, body force ------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_L_fp64(kernel):
+    g, op = pair((2, 2, 3), 3, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 10)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_inverse_mass_fp64(k):
+    g, op = pair((2, 1, 2), k)
+    R = inputs.uniform((op.mesh.Nc, 5, op.mesh.n ** 3), 11)
+    l2, mx = rel_err(g.inverse_mass(on_gpu(R)), op.mass_solve(R))
+    assert l2 < TOL64 and mx < TOL64
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_L_with_body_force_and_walls(kernel):
+    g, op = pair((2, 2, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
+                 body_force=(1.0, 0.0, 0.0), kernel=kernel)
+    U = inputs.channel_state(g.node_coords().cpu(), 3)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+# -- RK stages ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_rk_stage_fp64(kernel):
+    g, op = pair((2, 2, 2), 3, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 12)
+    dU = inputs.uniform(U.shape, 13)
+    dt = 1e-3
+    for stage in (0, 2):
+        Uo = g.empty_state()
+        dUg = on_gpu(dU)
+        g.rk_stage(stage, dt, 0.0, on_gpu(U), dUg, Uo)
+        dU_ref = ork.A[stage] * dU + dt * op.L(U)
+        U_ref = U + ork.B[stage] * dU_ref
+        assert max(rel_err(dUg, dU_ref)) < TOL64
+        assert max(rel_err(Uo, U_ref)) < TOL64
+
+
+def test_rk_stage_split_in_place_allowed_fused_rejected():
+    g, op = pair((2, 2, 2), 2, kernel=0)
+    U = on_gpu(inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 14))
+    dU = g.empty_residual()
+    g.rk_stage(0, 1e-3, 0.0, U, dU, U)
+    gf, _ = pair((2, 2, 2), 2, kernel=1)
+    with pytest.raises(api.DGCNSError) as ei:
+        gf.rk_stage(0, 1e-3, 0.0, U, dU, U)
+    assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_tgv_8cubed_ten_rk_steps_fp64(kernel):
+    """Taylor--Green 8^3, k = 3, one operator evaluation plus 10 RK(5,4) steps at CFL 0.4."""
+    g, op = pair((8, 8, 8), 3, kernel=kernel)
+    U0 = inputs.tgv_state(op.xyz)
+    ref, t2, tm = fp64_tol(op.L, U0)
+    assert t2 < 1e-10 and tm < 1e-9  # the conditioning itself is pinned
+    l2, mx = rel_err(g.apply(on_gpu(U0), op=api.OP_L), ref)
+    assert l2 < t2 and mx < tm, (l2, mx, t2, tm)
+    dt = api.cfl_dt(3, 2 * PI / 8, 1.0, 0.1, Cr=0.4, nu=1.0 / 1600)
+    Ug = on_gpu(U0)
+    g.rk_steps(10, dt, 0.0, Ug)
+    Ur = U0
+    for i in range(10):
+        Ur = ork.step(lambda V, t: op.L(V), Ur, dt, i * dt)
+    # the change of the state over 10 steps (50 evaluations of L): the per-evaluation
+    # rounding noise accumulates, so allow 3x the single-evaluation bound
+    l2, mx = rel_err(Ug - on_gpu(U0), Ur - U0)
+    assert l2 < 3 * t2 and mx < 3 * tm, (l2, mx)
+    l2, mx = rel_err(Ug, Ur)
+    assert l2 < TOL64 and mx < TOL64
+
+
+# -- diagnostics ---------------------------------------------------------------------------------------
+def test_diagnostics_fp64():
+    g, op = pair((4, 4, 4), 3)
+    U = inputs.tgv_state(op.xyz)
+    LU = op.L(U)
+    ref = odiag.diagnostics(op, U, LU).numpy()
+    out = g.diagnostics(on_gpu(U), on_gpu(LU))
+    assert np.allclose(out[:8], ref[:8], rtol=1e-12, atol=1e-14)
+    assert out[8] == 0
+
+
+def test_diagnostics_nonfinite_reported():
+    g, op = pair((2, 2, 2), 2)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 15)
+    U[1, 2, 3] = float("nan")
+    with pytest.raises(api.DGCNSError) as ei:
+        g.diagnostics(on_gpu(U))
+    assert ei.value.code == -5
+    assert g.diagnostics(on_gpu(U), check=False)[8] == 1
+
+
+# -- mixed precision ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_mixed_precision_error_bound(kernel):
+    """FP32 cell/face arithmetic: residual error of a few FP32 ulps of the state scale."""
+    g, op = pair((4, 4, 4), 3, precision=1, kernel=kernel)
+    U = inputs.tgv_state(op.xyz)
+    ref = op.L(U)
+    out = g.apply(on_gpu(U), op=api.OP_L)
+    assert out.dtype == torch.float32
+    l2, mx = rel_err(out, ref)
+    assert l2 < 2e-3 and mx < 2e-3, (l2, mx)
+
+
+# -- argument errors -------------------------------------------------------------------------------------
+def test_unsupported_configuration():
+    with pytest.raises(api.DGCNSError) as ei:
+        DGCNS((2, 2, 2), (0, 0, 0), (1, 1, 1), (1, 1, 1), 3, 9, 9)
+    assert ei.value.code == -2
+    with pytest.raises(api.DGCNSError) as ei:
+        DGCNS((2, 2, 2), (0, 0, 0), (1, 1, 1), (1, 1, 1), 3, 3, 3)
+    assert ei.value.code == -1
