@@ -199,8 +199,9 @@ def main():
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 arithmetic / f64 state", "data": "synthetic",
-           "config": {"workload": "Taylor-Green vortex 64^3 cells, k=3, nq_conv=5, nq_visc=4, RK(5,4), %s, %s kernel"
-                      % (args.precision, args.kernel), "cells": Nc, "nodes": nodes, "dofs": 5 * nodes,
+           "config": {"workload": "Taylor-Green vortex %d^3 cells, k=%d, nq_conv=%d, nq_visc=%d, RK(5,4), %s, %s kernel"
+                      % (cfg["ncells"][0], cfg["k"], cfg["nq_conv"], cfg["nq_visc"], args.precision, args.kernel),
+                      "cells": Nc, "nodes": nodes, "dofs": 5 * nodes,
                       "stages_timed": stages, "dt": dt,
                       "l2": "inputs larger than L2 (state %.0f MB per vector)" % (nodes * 40 / 1e6),
                       "parallelism": "replicas" if ws > 1 else "1 GPU"},

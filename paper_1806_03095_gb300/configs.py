@@ -26,6 +26,8 @@ def channel(N=32, k=3, precision=1, kernel=1, mapping=1):
 WORKLOADS = {
     "tgv8_k3": lambda **kw: tgv(8, 3, **kw),
     "tgv64_k3": lambda **kw: tgv(64, 3, **kw),
+    "tgv48_k3": lambda **kw: tgv(48, 3, **kw),
+    "tgv32_k3": lambda **kw: tgv(32, 3, **kw),
     "tgv40_k5": lambda **kw: tgv(40, 5, **kw),
     "tgv24_k4": lambda **kw: tgv(24, 4, **kw),
     "channel32_k3": lambda **kw: channel(32, 3, **kw),

@@ -6,27 +6,37 @@ namespace dgcns {
 
 // Offsets (in elements) of the 1D tables inside one contiguous table buffer.
 // Every table is computed on the host in FP64 and stored once as double and
-// once as float.  Matrices are row-major [rows][cols].
+// once as float.  The point sets (LGL nodes, Gauss points) are symmetric about
+// 1/2, so every 1D operator O (DOUT x DIN) satisfies
+// O[DOUT-1-q][DIN-1-i] = s O[q][i] with s = +1 (interpolation) or -1
+// (derivative); it is stored in even-odd form (Sec. 2.3, even-odd
+// decomposition): for q < ceil(DOUT/2), i < floor(DIN/2)
+//   a[q][i] = (O[q][i] + O[q][DIN-1-i]) / 2,  b[q][i] = (O[q][i] - O[q][DIN-1-i]) / 2,
+//   c[q]    = O[q][DIN/2] (middle column, DIN odd; else 0).
+enum EoOp { EO_SC, EO_SCT, EO_DC, EO_DCT, EO_SV, EO_SVT, EO_DV, EO_DVT, EO_SMI, EO_SMIT, EO_SM, EO_NOPS };
+
+constexpr int eo_size(int dout, int din) { return ((dout + 1) / 2) * (din / 2) * 2 + (dout + 1) / 2; }
+
 struct TableLayout {
   int N, QC, QV;
-  int Sc, Dc;   // Sc[QC][N]  l_i(x_q), convective Gauss points; Dc[QC][QC] collocation derivative
-  int Sv, Dv;   // Sv[QV][N], Dv[QV][QV]  same for the viscous points
-  int Sm, Smi;  // Sm[N][N] at the N = k+1 mass points; Smi = Sm^-1
-  int wc, wv, wm;  // 1D Gauss weights on [0,1]
-  int dl0, dl1;    // dl0[i] = l_i'(0), dl1[i] = l_i'(1)
+  int eo[EO_NOPS];  // offsets of the even-odd operators
+  int wc, wv, wm;   // 1D Gauss weights on [0,1]
+  int dl0, dl1;     // dl0[i] = l_i'(0), dl1[i] = l_i'(1)
   int total;
 };
 
 constexpr TableLayout make_layout(int N, int QC, int QV) {
   TableLayout L{};
-  L.N = N; L.QC = QC; L.QV = QV;
+  L.N = N;
+  L.QC = QC;
+  L.QV = QV;
   int o = 0;
-  L.Sc = o; o += QC * N;
-  L.Dc = o; o += QC * QC;
-  L.Sv = o; o += QV * N;
-  L.Dv = o; o += QV * QV;
-  L.Sm = o; o += N * N;
-  L.Smi = o; o += N * N;
+  const int dims[EO_NOPS][2] = {{QC, N}, {N, QC}, {QC, QC}, {QC, QC}, {QV, N}, {N, QV},
+                                {QV, QV}, {QV, QV}, {N, N},   {N, N},   {N, N}};
+  for (int k = 0; k < EO_NOPS; ++k) {
+    L.eo[k] = o;
+    o += eo_size(dims[k][0], dims[k][1]);
+  }
   L.wc = o; o += QC;
   L.wv = o; o += QV;
   L.wm = o; o += N;
@@ -46,6 +56,8 @@ struct KParams {
   int has_bf;           // body force present
   double gamma, mu, lam, cv;
   double Tw;            // wall temperature
+  double rho_ref;       // reference state (rho_ref, 0, 0, 0, rho_ref c_v T_w): the kernels carry U - U_ref
+  double rhoE_ref;
   double h[3];          // affine cell extents
   double bf[3];         // body force vector
   double A, B, dt;      // 2N stage coefficients (out_mode 2)

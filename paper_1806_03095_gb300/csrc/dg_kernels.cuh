@@ -27,35 +27,39 @@ namespace dgcns {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Tab {
-  const T *Sc, *Dc, *Sv, *Dv, *Sm, *Smi, *wc, *wv, *wm, *dl0, *dl1;
+  const T *eSc, *eScT, *eDc, *eDcT, *eSv, *eSvT, *eDv, *eDvT, *eSmi, *eSmiT, *eSm;
+  const T *wc, *wv, *wm, *dl0, *dl1;
 };
 
 template <typename T, int N, int QC, int QV>
 __device__ __forceinline__ Tab<T> load_tables(const T* __restrict__ g, T* s) {
-  const TableLayout L = make_layout(N, QC, QV);
+  constexpr TableLayout L = make_layout(N, QC, QV);
   for (int i = threadIdx.x; i < L.total; i += blockDim.x) s[i] = g[i];
   Tab<T> t;
-  t.Sc = s + L.Sc; t.Dc = s + L.Dc; t.Sv = s + L.Sv; t.Dv = s + L.Dv;
-  t.Sm = s + L.Sm; t.Smi = s + L.Smi; t.wc = s + L.wc; t.wv = s + L.wv; t.wm = s + L.wm;
-  t.dl0 = s + L.dl0; t.dl1 = s + L.dl1;
+  t.eSc = s + L.eo[EO_SC]; t.eScT = s + L.eo[EO_SCT]; t.eDc = s + L.eo[EO_DC]; t.eDcT = s + L.eo[EO_DCT];
+  t.eSv = s + L.eo[EO_SV]; t.eSvT = s + L.eo[EO_SVT]; t.eDv = s + L.eo[EO_DV]; t.eDvT = s + L.eo[EO_DVT];
+  t.eSmi = s + L.eo[EO_SMI]; t.eSmiT = s + L.eo[EO_SMIT]; t.eSm = s + L.eo[EO_SM];
+  t.wc = s + L.wc; t.wv = s + L.wv; t.wm = s + L.wm; t.dl0 = s + L.dl0; t.dl1 = s + L.dl1;
   return t;
 }
 
 template <int N, int QC, int QV>
 constexpr int table_elems() {
-  return ((QC * N + QC * QC + QV * N + QV * QV + 2 * N * N + QC + QV + 3 * N) + 3) & ~3;
+  return make_layout(N, QC, QV).total;
 }
 
 // ---------------------------------------------------------------------------
-// 1D sweep: apply the matrix M along axis AX of nblk arrays of shape
-// (D2, D1, D0) (D0 fastest, arrays contiguous one after the other).  The
-// axis extent DIN becomes DOUT.  M is [DOUT][DIN] (TR = false) or applied
-// transposed from storage [DIN][DOUT] (TR = true).  ACC adds into out.
+// 1D sweep with even-odd decomposition: apply the operator O (DOUT x DIN, in
+// the even-odd form above, symmetry SYM = +1 or -1) along axis AX of nblk
+// arrays of shape (D2, D1, D0) (D0 fastest, arrays contiguous one after the
+// other).  The axis extent DIN becomes DOUT.  One thread per line, the line in
+// registers, the operator broadcast from shared memory.  ACC adds into out.
 // ---------------------------------------------------------------------------
-template <typename T, int AX, int D0, int D1, int D2, int DOUT, bool TR, bool ACC>
-__device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M,
+template <typename T, int AX, int D0, int D1, int D2, int DOUT, int SYM, bool ACC>
+__device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ E,
                                       int nblk) {
   constexpr int DIN = AX == 0 ? D0 : (AX == 1 ? D1 : D2);
+  constexpr int IH = DIN / 2, OH = (DOUT + 1) / 2;
   constexpr int O0 = AX == 0 ? DOUT : D0;
   constexpr int O1 = AX == 1 ? DOUT : D1;
   constexpr int O2 = AX == 2 ? DOUT : D2;
@@ -63,6 +67,9 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
   constexpr int NL = ISZ / DIN;
   constexpr int IST = AX == 0 ? 1 : (AX == 1 ? D0 : D0 * D1);
   constexpr int OST = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
+  const T* __restrict__ A = E;
+  const T* __restrict__ B = E + OH * IH;
+  const T* __restrict__ C = E + 2 * OH * IH;
   for (int l = threadIdx.x; l < nblk * NL; l += blockDim.x) {
     const int blk = l / NL, r = l - blk * NL;
     int ib, ob;
@@ -79,18 +86,36 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
     }
     const T* ip = in + blk * ISZ + ib;
     T* op = out + blk * OSZ + ob;
-    T x[DIN];
+    T xe[IH], xo[IH];
+    T xm = T(0);
 #pragma unroll
-    for (int i = 0; i < DIN; ++i) x[i] = ip[i * IST];
+    for (int i = 0; i < IH; ++i) {
+      const T lo = ip[i * IST], hi = ip[(DIN - 1 - i) * IST];
+      xe[i] = lo + hi;
+      xo[i] = lo - hi;
+    }
+    if (DIN & 1) xm = ip[IH * IST];
 #pragma unroll
-    for (int o = 0; o < DOUT; ++o) {
-      T acc = (TR ? M[o] : M[o * DIN]) * x[0];
+    for (int q = 0; q < OH; ++q) {
+      T e = (DIN & 1) ? C[q] * xm : T(0);
+      T o = T(0);
 #pragma unroll
-      for (int i = 1; i < DIN; ++i) acc += (TR ? M[i * DOUT + o] : M[o * DIN + i]) * x[i];
-      if (ACC)
-        op[o * OST] += acc;
-      else
-        op[o * OST] = acc;
+      for (int i = 0; i < IH; ++i) {
+        e += A[q * IH + i] * xe[i];
+        o += B[q * IH + i] * xo[i];
+      }
+      if ((DOUT & 1) && q == OH - 1) {
+        if (ACC) op[q * OST] += e + o; else op[q * OST] = e + o;
+      } else {
+        const T lo = e + o, hi = SYM > 0 ? e - o : o - e;
+        if (ACC) {
+          op[q * OST] += lo;
+          op[(DOUT - 1 - q) * OST] += hi;
+        } else {
+          op[q * OST] = lo;
+          op[(DOUT - 1 - q) * OST] = hi;
+        }
+      }
     }
   }
 }
@@ -99,34 +124,46 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
 // Pointwise physics (Eq. CompressibleNavierStokesFluxes).  F[c][j], c the
 // conserved component, j the physical direction.
 // ---------------------------------------------------------------------------
+//
+// The kernels carry the state as deviations dU = U - U_ref from the constant
+// reference U_ref = (rho_r, 0, 0, 0, rho_r c_v T_0) (T_0 the reference and wall
+// temperature).  Jumps are dU- - dU+, the momentum flux uses the pressure
+// deviation dp = p - p_r (p_r = (gamma-1) rho_r c_v T_0): the constant flux
+// p_r I has zero residual on every element (free-stream identity), so this is
+// the same operator, while FP32 arithmetic keeps the O(1) fluctuations instead
+// of rounding them against rho E ~ 10^2..10^5.
 template <typename T>
 struct PhysT {
   T gamma, gm1, mu, lam_cv;  // lam_cv = lambda / c_v
+  T rho_r, rhoE_r, p_r, H_r; // reference density, energy, pressure, rhoE_r + p_r
+  T cvTw2;                   // 2 c_v T_wall
 };
 
+// pressure deviation p - p_r = (gamma-1)(d(rho E) - |m|^2/(2 rho))
 template <typename T>
-__device__ __forceinline__ T pressure(const T u[5], T rinv, T gm1) {
+__device__ __forceinline__ T pressure_dev(const T u[5], T rinv, T gm1) {
   return gm1 * (u[4] - T(0.5) * rinv * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]));
 }
 
-// Convective flux along one direction j: F_c[.][j]
+// Convective flux along direction j, F_c[.][j], minus the constant p_r I:
+// (m_j, m v_j + dp e_j, (H_r + d(rho E) + dp) v_j)
 template <typename T>
-__device__ __forceinline__ void conv_flux_dir(const T u[5], T rinv, T p, int j, T f[5]) {
+__device__ __forceinline__ void conv_flux_dir(const T u[5], T rinv, T dp, T H_r, int j, T f[5]) {
   const T vj = u[1 + j] * rinv;
   f[0] = u[1 + j];
   f[1] = u[1] * vj;
   f[2] = u[2] * vj;
   f[3] = u[3] * vj;
-  f[1 + j] += p;
-  f[4] = (u[4] + p) * vj;
+  f[1 + j] += dp;
+  f[4] = (H_r + u[4] + dp) * vj;
 }
 
-// Viscous flux F_v(U, G) with G[c][a] the (physical) gradient argument.
+// Viscous flux F_v(U, G) from deviations u and the (physical) gradient argument G[c][a].
 template <typename T>
 __device__ __forceinline__ void visc_flux(const T u[5], const T G[5][3], const PhysT<T>& ph, T F[5][3]) {
-  const T rinv = T(1) / u[0];
+  const T rinv = T(1) / (ph.rho_r + u[0]);
   const T v0 = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
-  const T E = u[4] * rinv;
+  const T E = (ph.rhoE_r + u[4]) * rinv;
   T gu[3][3];
   const T v[3] = {v0, v1, v2};
 #pragma unroll
@@ -152,17 +189,18 @@ __device__ __forceinline__ void visc_flux(const T u[5], const T G[5][3], const P
   }
 }
 
-// Exterior state on an isothermal no-slip wall: rho+ = rho-, u+ = -u-, T+ = 2 T_w - T-.
+// Exterior state on an isothermal no-slip wall: rho+ = rho-, u+ = -u-, T+ = 2 T_w - T-,
+// i.e. rho E+ = 2 rho c_v T_w - rho E- + rho |u|^2, written for deviations
+// (rho E_r = rho_r c_v T_w):  d(rho E)+ = 2 c_v T_w d(rho) - d(rho E)- + |m|^2/rho.
 template <typename T>
-__device__ __forceinline__ void wall_ghost(const T um[5], T cvTw2, T up[5]) {
-  const T rinv = T(1) / um[0];
-  const T ke = T(0.5) * rinv * (um[1] * um[1] + um[2] * um[2] + um[3] * um[3]);  // rho |u|^2/2
-  const T cvT = (um[4] - ke) * rinv;                                               // c_v T-
+__device__ __forceinline__ void wall_ghost(const T um[5], const PhysT<T>& ph, T up[5]) {
+  const T rinv = T(1) / (ph.rho_r + um[0]);
+  const T ke2 = rinv * (um[1] * um[1] + um[2] * um[2] + um[3] * um[3]);  // rho |u|^2
   up[0] = um[0];
   up[1] = -um[1];
   up[2] = -um[2];
   up[3] = -um[3];
-  up[4] = um[0] * (cvTw2 - cvT) + ke;
+  up[4] = ph.cvTw2 * um[0] - um[4] + ke2;
 }
 
 // ---------------------------------------------------------------------------
@@ -211,11 +249,11 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
     T* F2 = ar + 2 * CB * 5 * P;
     T* G = ar + 3 * CB * 5 * P;
     // interpolate to the convective Gauss grid (Eq. SumFactorization)
-    sweep<T, 0, N, N, N, QC, false, false>(su, F1, tb.Sc, nbl);
+    sweep<T, 0, N, N, N, QC, 1, false>(su, F1, tb.eSc, nbl);
     __syncthreads();
-    sweep<T, 1, QC, N, N, QC, false, false>(F1, F2, tb.Sc, nbl);
+    sweep<T, 1, QC, N, N, QC, 1, false>(F1, F2, tb.eSc, nbl);
     __syncthreads();
-    sweep<T, 2, QC, QC, N, QC, false, false>(F2, F0, tb.Sc, nbl);
+    sweep<T, 2, QC, QC, N, QC, 1, false>(F2, F0, tb.eSc, nbl);
     __syncthreads();
     // pointwise: contravariant flux  -F_c J^{-T} |J| w  (minus sign of the weak form)
     for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
@@ -225,13 +263,13 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       T u[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) u[c] = F0[(e * 5 + c) * P + p];
-      const T rinv = T(1) / u[0];
-      const T pr = pressure(u, rinv, ph.gm1);
+      const T rinv = T(1) / (ph.rho_r + u[0]);
+      const T dp = pressure_dev(u, rinv, ph.gm1);
       T* Fd[3] = {F0, F1, F2};
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         T f[5];
-        conv_flux_dir(u, rinv, pr, j, f);
+        conv_flux_dir(u, rinv, dp, ph.H_r, j, f);
         const T s = -w * hinv[j];
 #pragma unroll
         for (int c = 0; c < 5; ++c) Fd[j][(e * 5 + c) * P + p] = s * f[c];
@@ -239,18 +277,18 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
     }
     __syncthreads();
     // G = sum_d D_d^T Ft_d  (test with grad V in the collocation basis)
-    sweep<T, 0, QC, QC, QC, QC, true, false>(F0, G, tb.Dc, nbl);
+    sweep<T, 0, QC, QC, QC, QC, -1, false>(F0, G, tb.eDcT, nbl);
     __syncthreads();
-    sweep<T, 1, QC, QC, QC, QC, true, true>(F1, G, tb.Dc, nbl);
+    sweep<T, 1, QC, QC, QC, QC, -1, true>(F1, G, tb.eDcT, nbl);
     __syncthreads();
-    sweep<T, 2, QC, QC, QC, QC, true, true>(F2, G, tb.Dc, nbl);
+    sweep<T, 2, QC, QC, QC, QC, -1, true>(F2, G, tb.eDcT, nbl);
     __syncthreads();
     // back to the nodes: S^T along z, y, x
-    sweep<T, 2, QC, QC, QC, N, true, false>(G, F0, tb.Sc, nbl);
+    sweep<T, 2, QC, QC, QC, N, 1, false>(G, F0, tb.eScT, nbl);
     __syncthreads();
-    sweep<T, 1, QC, QC, N, N, true, false>(F0, F1, tb.Sc, nbl);
+    sweep<T, 1, QC, QC, N, N, 1, false>(F0, F1, tb.eScT, nbl);
     __syncthreads();
-    sweep<T, 0, QC, N, N, N, true, true>(F1, sr, tb.Sc, nbl);
+    sweep<T, 0, QC, N, N, N, 1, true>(F1, sr, tb.eScT, nbl);
     __syncthreads();
   }
   if (kp.visc) {
@@ -259,16 +297,16 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
     T* V1 = ar + CB * 5 * P;
     T* V2 = ar + 2 * CB * 5 * P;
     T* V3 = ar + 3 * CB * 5 * P;
-    sweep<T, 0, N, N, N, QV, false, false>(su, V1, tb.Sv, nbl);
+    sweep<T, 0, N, N, N, QV, 1, false>(su, V1, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 1, QV, N, N, QV, false, false>(V1, V2, tb.Sv, nbl);
+    sweep<T, 1, QV, N, N, QV, 1, false>(V1, V2, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 2, QV, QV, N, QV, false, false>(V2, V0, tb.Sv, nbl);
+    sweep<T, 2, QV, QV, N, QV, 1, false>(V2, V0, tb.eSv, nbl);
     __syncthreads();
     // reference gradients by collocation
-    sweep<T, 0, QV, QV, QV, QV, false, false>(V0, V1, tb.Dv, nbl);
-    sweep<T, 1, QV, QV, QV, QV, false, false>(V0, V2, tb.Dv, nbl);
-    sweep<T, 2, QV, QV, QV, QV, false, false>(V0, V3, tb.Dv, nbl);
+    sweep<T, 0, QV, QV, QV, QV, -1, false>(V0, V1, tb.eDv, nbl);
+    sweep<T, 1, QV, QV, QV, QV, -1, false>(V0, V2, tb.eDv, nbl);
+    sweep<T, 2, QV, QV, QV, QV, -1, false>(V0, V3, tb.eDv, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
       const int e = idx / P, p = idx - e * P;
@@ -291,17 +329,17 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       }
     }
     __syncthreads();
-    sweep<T, 0, QV, QV, QV, QV, true, false>(V1, V0, tb.Dv, nbl);
+    sweep<T, 0, QV, QV, QV, QV, -1, false>(V1, V0, tb.eDvT, nbl);
     __syncthreads();
-    sweep<T, 1, QV, QV, QV, QV, true, true>(V2, V0, tb.Dv, nbl);
+    sweep<T, 1, QV, QV, QV, QV, -1, true>(V2, V0, tb.eDvT, nbl);
     __syncthreads();
-    sweep<T, 2, QV, QV, QV, QV, true, true>(V3, V0, tb.Dv, nbl);
+    sweep<T, 2, QV, QV, QV, QV, -1, true>(V3, V0, tb.eDvT, nbl);
     __syncthreads();
-    sweep<T, 2, QV, QV, QV, N, true, false>(V0, V1, tb.Sv, nbl);
+    sweep<T, 2, QV, QV, QV, N, 1, false>(V0, V1, tb.eSvT, nbl);
     __syncthreads();
-    sweep<T, 1, QV, QV, N, N, true, false>(V1, V2, tb.Sv, nbl);
+    sweep<T, 1, QV, QV, N, N, 1, false>(V1, V2, tb.eSvT, nbl);
     __syncthreads();
-    sweep<T, 0, QV, N, N, N, true, true>(V2, sr, tb.Sv, nbl);
+    sweep<T, 0, QV, N, N, N, 1, true>(V2, sr, tb.eSvT, nbl);
     __syncthreads();
   }
 }
@@ -326,7 +364,6 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
   const int idm = s ? N - 1 : 0, idp = s ? 0 : N - 1;
   const T* dlm = s ? tb.dl1 : tb.dl0;  // l_i' at the own face
   const T* dlp = s ? tb.dl0 : tb.dl1;  // l_i' at the neighbour's face
-  const T cvTw2 = T(2.0 * kp.cv * kp.Tw);
   const int nbl = nb * 5;
 
   if (kp.conv) {
@@ -342,13 +379,13 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
       Lp[idx] = wall[e] ? T(0) : sn[ec * N3 + face_node<N>(d, idp, j % N, j / N)];
     }
     __syncthreads();
-    sweep<T, 0, N, N, 1, QC, false, false>(Lm, Tm, tb.Sc, nbl);
+    sweep<T, 0, N, N, 1, QC, 1, false>(Lm, Tm, tb.eSc, nbl);
     __syncthreads();
-    sweep<T, 1, QC, N, 1, QC, false, false>(Tm, Um, tb.Sc, nbl);
+    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Um, tb.eSc, nbl);
     __syncthreads();
-    sweep<T, 0, N, N, 1, QC, false, false>(Lp, Tm, tb.Sc, nbl);
+    sweep<T, 0, N, N, 1, QC, 1, false>(Lp, Tm, tb.eSc, nbl);
     __syncthreads();
-    sweep<T, 1, QC, N, 1, QC, false, false>(Tm, Up, tb.Sc, nbl);
+    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Up, tb.eSc, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
       const int e = idx / P, p = idx - e * P;
@@ -359,23 +396,23 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
         um[c] = Um[(e * 5 + c) * P + p];
         up[c] = Up[(e * 5 + c) * P + p];
       }
-      if (wall[e]) wall_ghost(um, cvTw2, up);
-      const T rm = T(1) / um[0], rp = T(1) / up[0];
-      const T pm = pressure(um, rm, ph.gm1), pp = pressure(up, rp, ph.gm1);
-      const T lm = sqrt(um[1] * um[1] + um[2] * um[2] + um[3] * um[3]) * rm + sqrt(fabs(ph.gamma * pm * rm));
-      const T lp = sqrt(up[1] * up[1] + up[2] * up[2] + up[3] * up[3]) * rp + sqrt(fabs(ph.gamma * pp * rp));
+      if (wall[e]) wall_ghost(um, ph, up);
+      const T rm = T(1) / (ph.rho_r + um[0]), rp = T(1) / (ph.rho_r + up[0]);
+      const T pm = pressure_dev(um, rm, ph.gm1), pp = pressure_dev(up, rp, ph.gm1);
+      const T lm = sqrt(um[1] * um[1] + um[2] * um[2] + um[3] * um[3]) * rm + sqrt(fabs(ph.gamma * (ph.p_r + pm) * rm));
+      const T lp = sqrt(up[1] * up[1] + up[2] * up[2] + up[3] * up[3]) * rp + sqrt(fabs(ph.gamma * (ph.p_r + pp) * rp));
       const T lam = lm > lp ? lm : lp;
       T fm[5], fp[5];
-      conv_flux_dir(um, rm, pm, d, fm);
-      conv_flux_dir(up, rp, pp, d, fp);
+      conv_flux_dir(um, rm, pm, ph.H_r, d, fm);
+      conv_flux_dir(up, rp, pp, ph.H_r, d, fp);
 #pragma unroll
       for (int c = 0; c < 5; ++c)
         Um[(e * 5 + c) * P + p] = w * (T(0.5) * sgn * (fm[c] + fp[c]) + T(0.5) * lam * (um[c] - up[c]));
     }
     __syncthreads();
-    sweep<T, 1, QC, QC, 1, N, true, false>(Um, Tm, tb.Sc, nbl);
+    sweep<T, 1, QC, QC, 1, N, 1, false>(Um, Tm, tb.eScT, nbl);
     __syncthreads();
-    sweep<T, 0, QC, N, 1, N, true, false>(Tm, Lm, tb.Sc, nbl);
+    sweep<T, 0, QC, N, 1, N, 1, false>(Tm, Lm, tb.eScT, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
       const int ec = idx / N2, j = idx - ec * N2;
@@ -422,26 +459,26 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
     }
     __syncthreads();
     // values and normal derivatives to the face Gauss points
-    sweep<T, 0, N, N, 1, QV, false, false>(Lm, Tm, tb.Sv, nbl);
+    sweep<T, 0, N, N, 1, QV, 1, false>(Lm, Tm, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Um, tb.Sv, nbl);
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Um, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 0, N, N, 1, QV, false, false>(Lp, Tm, tb.Sv, nbl);
+    sweep<T, 0, N, N, 1, QV, 1, false>(Lp, Tm, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Up, tb.Sv, nbl);
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Up, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 0, N, N, 1, QV, false, false>(Dm, Tm, tb.Sv, nbl);
+    sweep<T, 0, N, N, 1, QV, 1, false>(Dm, Tm, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Gdm, tb.Sv, nbl);
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdm, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 0, N, N, 1, QV, false, false>(Dp, Tm, tb.Sv, nbl);
+    sweep<T, 0, N, N, 1, QV, 1, false>(Dp, Tm, tb.eSv, nbl);
     __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, false, false>(Tm, Gdp, tb.Sv, nbl);
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdp, tb.eSv, nbl);
     // tangential derivatives by collocation on the face grid
-    sweep<T, 0, QV, QV, 1, QV, false, false>(Um, G1m, tb.Dv, nbl);
-    sweep<T, 1, QV, QV, 1, QV, false, false>(Um, G2m, tb.Dv, nbl);
-    sweep<T, 0, QV, QV, 1, QV, false, false>(Up, G1p, tb.Dv, nbl);
-    sweep<T, 1, QV, QV, 1, QV, false, false>(Up, G2p, tb.Dv, nbl);
+    sweep<T, 0, QV, QV, 1, QV, -1, false>(Um, G1m, tb.eDv, nbl);
+    sweep<T, 1, QV, QV, 1, QV, -1, false>(Um, G2m, tb.eDv, nbl);
+    sweep<T, 0, QV, QV, 1, QV, -1, false>(Up, G1p, tb.eDv, nbl);
+    sweep<T, 1, QV, QV, 1, QV, -1, false>(Up, G2p, tb.eDv, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
       const int e = idx / P, p = idx - e * P;
@@ -460,7 +497,7 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
         Gp[c][d] = Gdp[o + c * P] * hinv[d];
       }
       if (wall[e]) {
-        wall_ghost(um, cvTw2, up);
+        wall_ghost(um, ph, up);
 #pragma unroll
         for (int c = 0; c < 5; ++c)
 #pragma unroll
@@ -497,18 +534,18 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
     }
     __syncthreads();
     // value test + tangential gradient tests on the face grid
-    sweep<T, 0, QV, QV, 1, QV, true, true>(G1m, Um, tb.Dv, nbl);
+    sweep<T, 0, QV, QV, 1, QV, -1, true>(G1m, Um, tb.eDvT, nbl);
     __syncthreads();
-    sweep<T, 1, QV, QV, 1, QV, true, true>(G2m, Um, tb.Dv, nbl);
+    sweep<T, 1, QV, QV, 1, QV, -1, true>(G2m, Um, tb.eDvT, nbl);
     __syncthreads();
-    sweep<T, 1, QV, QV, 1, N, true, false>(Um, Tm, tb.Sv, nbl);
+    sweep<T, 1, QV, QV, 1, N, 1, false>(Um, Tm, tb.eSvT, nbl);
     __syncthreads();
-    sweep<T, 0, QV, N, 1, N, true, false>(Tm, Lm, tb.Sv, nbl);
+    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Lm, tb.eSvT, nbl);
     __syncthreads();
     // normal gradient test
-    sweep<T, 1, QV, QV, 1, N, true, false>(Gdm, Tm, tb.Sv, nbl);
+    sweep<T, 1, QV, QV, 1, N, 1, false>(Gdm, Tm, tb.eSvT, nbl);
     __syncthreads();
-    sweep<T, 0, QV, N, 1, N, true, false>(Tm, Dm, tb.Sv, nbl);
+    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Dm, tb.eSvT, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
       const int ec = idx / N2, j = idx - ec * N2;
@@ -541,11 +578,11 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
   T* A = ma;
   T* B = ma + CB * 5 * N3;
   const T detJ = T(kp.h[0] * kp.h[1] * kp.h[2]);
-  sweep<T, 0, N, N, N, N, true, false>(sr, A, tb.Smi, nbl);
+  sweep<T, 0, N, N, N, N, 1, false>(sr, A, tb.eSmiT, nbl);
   __syncthreads();
-  sweep<T, 1, N, N, N, N, true, false>(A, B, tb.Smi, nbl);
+  sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmiT, nbl);
   __syncthreads();
-  sweep<T, 2, N, N, N, N, true, false>(B, A, tb.Smi, nbl);
+  sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmiT, nbl);
   __syncthreads();
   const T sg = negate ? T(-1) : T(1);
   for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
@@ -554,35 +591,35 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
     A[idx] *= sg / w;
   }
   __syncthreads();
-  sweep<T, 0, N, N, N, N, false, false>(A, B, tb.Smi, nbl);
+  sweep<T, 0, N, N, N, N, 1, false>(A, B, tb.eSmi, nbl);
   __syncthreads();
-  sweep<T, 1, N, N, N, N, false, false>(B, A, tb.Smi, nbl);
+  sweep<T, 1, N, N, N, N, 1, false>(B, A, tb.eSmi, nbl);
   __syncthreads();
-  sweep<T, 2, N, N, N, N, false, false>(A, sr, tb.Smi, nbl);
+  sweep<T, 2, N, N, N, N, 1, false>(A, sr, tb.eSmi, nbl);
   __syncthreads();
   if (add_force) {
     // F_rhs = (0, f, f.u): momentum rows are the constant f (S^{-1} 1 = 1), energy row S^{-1}(f . u)(x_q)
     const T f0 = T(kp.bf[0]), f1 = T(kp.bf[1]), f2 = T(kp.bf[2]);
     // interpolate rho and momenta (components 0..3) to the mass points
     for (int e = 0; e < nb; ++e) {
-      sweep<T, 0, N, N, N, N, false, false>(su + e * 5 * N3, A + e * 4 * N3, tb.Sm, 4);
+      sweep<T, 0, N, N, N, N, 1, false>(su + e * 5 * N3, A + e * 4 * N3, tb.eSm, 4);
     }
     __syncthreads();
-    for (int e = 0; e < nb; ++e) sweep<T, 1, N, N, N, N, false, false>(A + e * 4 * N3, B + e * 4 * N3, tb.Sm, 4);
+    for (int e = 0; e < nb; ++e) sweep<T, 1, N, N, N, N, 1, false>(A + e * 4 * N3, B + e * 4 * N3, tb.eSm, 4);
     __syncthreads();
-    for (int e = 0; e < nb; ++e) sweep<T, 2, N, N, N, N, false, false>(B + e * 4 * N3, A + e * 4 * N3, tb.Sm, 4);
+    for (int e = 0; e < nb; ++e) sweep<T, 2, N, N, N, N, 1, false>(B + e * 4 * N3, A + e * 4 * N3, tb.eSm, 4);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
       const int e = idx / N3, p = idx - e * N3;
       const T* a = A + e * 4 * N3;
-      B[idx] = (f0 * a[N3 + p] + f1 * a[2 * N3 + p] + f2 * a[3 * N3 + p]) / a[p];
+      B[idx] = (f0 * a[N3 + p] + f1 * a[2 * N3 + p] + f2 * a[3 * N3 + p]) / (T(kp.rho_ref) + a[p]);
     }
     __syncthreads();
-    sweep<T, 0, N, N, N, N, false, false>(B, A, tb.Smi, nb);
+    sweep<T, 0, N, N, N, N, 1, false>(B, A, tb.eSmi, nb);
     __syncthreads();
-    sweep<T, 1, N, N, N, N, false, false>(A, B, tb.Smi, nb);
+    sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmi, nb);
     __syncthreads();
-    sweep<T, 2, N, N, N, N, false, false>(B, A, tb.Smi, nb);
+    sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmi, nb);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
       const int e = idx / N3, p = idx - e * N3;

@@ -32,6 +32,11 @@ constexpr size_t op_smem_bytes() {
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
 }
 
+// component c of the reference state U_ref = (rho_r, 0, 0, 0, rho_r c_v T_0)
+__device__ __forceinline__ double ref_of(const KParams& kp, int c) {
+  return c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0);
+}
+
 // ---------------------------------------------------------------------------
 // Generic operator kernel.  CELL: cell integrals; FACE: the 6 face integrals of
 // every cell; MASS: L = M^{-1}(-R + F_rhs).  Without CELL the partial residual
@@ -67,12 +72,17 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
   ph.gm1 = T(kp.gamma - 1.0);
   ph.mu = T(kp.mu);
   ph.lam_cv = T(kp.lam / kp.cv);
+  ph.rho_r = T(kp.rho_ref);
+  ph.rhoE_r = T(kp.rhoE_ref);
+  ph.p_r = T((kp.gamma - 1.0) * kp.rhoE_ref);
+  ph.H_r = T(kp.gamma * kp.rhoE_ref);
+  ph.cvTw2 = T(2.0 * kp.cv * kp.Tw);
 
   const size_t base = (size_t)e0 * 5 * N3;
   const int nvals = nb * 5 * N3;
   const bool need_u = CELL || FACE || (MASS && kp.has_bf);
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    if (need_u) su[i] = T(U[base + i]);
+    if (need_u) su[i] = T(U[base + i] - ref_of(kp, (i / N3) % 5));
     sr[i] = CELL ? T(0) : Rin[base + i];
   }
   __syncthreads();
@@ -102,7 +112,7 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
         __syncthreads();
         for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
           const int e = i / (5 * N3);
-          if (!wall[e]) sn[i] = T(U[(size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3)]);
+          if (!wall[e]) sn[i] = T(U[(size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3)] - ref_of(kp, (i / N3) % 5));
         }
         __syncthreads();
         if (d == 0) face_terms<T, N, QC, QV, CB, 0>(su, sn, wall, tau_f, sr, ar, tb, kp, ph, nb, s);
@@ -164,18 +174,18 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
     }
     __syncthreads();
     const int nbl = nb * 5;
-    sweep<double, 0, N, N, N, QC, false, false>(su, V1, tb.Sc, nbl);
+    sweep<double, 0, N, N, N, QC, 1, false>(su, V1, tb.eSc, nbl);
     __syncthreads();
-    sweep<double, 1, QC, N, N, QC, false, false>(V1, V2, tb.Sc, nbl);
+    sweep<double, 1, QC, N, N, QC, 1, false>(V1, V2, tb.eSc, nbl);
     __syncthreads();
-    sweep<double, 2, QC, QC, N, QC, false, false>(V2, V0, tb.Sc, nbl);
+    sweep<double, 2, QC, QC, N, QC, 1, false>(V2, V0, tb.eSc, nbl);
     __syncthreads();
     if (LU) {
-      sweep<double, 0, N, N, N, QC, false, false>(sl, V1, tb.Sc, nbl);
+      sweep<double, 0, N, N, N, QC, 1, false>(sl, V1, tb.eSc, nbl);
       __syncthreads();
-      sweep<double, 1, QC, N, N, QC, false, false>(V1, V2, tb.Sc, nbl);
+      sweep<double, 1, QC, N, N, QC, 1, false>(V1, V2, tb.eSc, nbl);
       __syncthreads();
-      sweep<double, 2, QC, QC, N, QC, false, false>(V2, L0, tb.Sc, nbl);
+      sweep<double, 2, QC, QC, N, QC, 1, false>(V2, L0, tb.eSc, nbl);
       __syncthreads();
     }
     const double detJ = kp.h[0] * kp.h[1] * kp.h[2];
@@ -199,9 +209,9 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
       __syncthreads();
-      if (j == 0) sweep<double, 0, QC, QC, QC, QC, false, false>(V0, V1, tb.Dc, nbl);
-      if (j == 1) sweep<double, 1, QC, QC, QC, QC, false, false>(V0, V1, tb.Dc, nbl);
-      if (j == 2) sweep<double, 2, QC, QC, QC, QC, false, false>(V0, V1, tb.Dc, nbl);
+      if (j == 0) sweep<double, 0, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+      if (j == 1) sweep<double, 1, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+      if (j == 2) sweep<double, 2, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
       __syncthreads();
       for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
         const int e = idx / P, p = idx - e * P;
@@ -221,11 +231,11 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
     }
     __syncthreads();
     // conservation totals with the k+1 point rule: int U = sum_q U(x_q) |J| w_q
-    sweep<double, 0, N, N, N, N, false, false>(su, V1, tb.Sm, nbl);
+    sweep<double, 0, N, N, N, N, 1, false>(su, V1, tb.eSm, nbl);
     __syncthreads();
-    sweep<double, 1, N, N, N, N, false, false>(V1, V2, tb.Sm, nbl);
+    sweep<double, 1, N, N, N, N, 1, false>(V1, V2, tb.eSm, nbl);
     __syncthreads();
-    sweep<double, 2, N, N, N, N, false, false>(V2, V1, tb.Sm, nbl);
+    sweep<double, 2, N, N, N, N, 1, false>(V2, V1, tb.eSm, nbl);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
       const int c = (idx / N3) % 5, p = idx % N3;

@@ -147,27 +147,73 @@ bool invert(std::vector<double>& A, int n) {
   return true;
 }
 
+// Make a point set exactly symmetric about 1/2 (x[n-1-i] = 1 - x[i]) so that the
+// even-odd form of every 1D operator is exact.
+void symmetrize(std::vector<double>& x, std::vector<double>* w = nullptr) {
+  const int n = (int)x.size();
+  for (int i = 0; i < n / 2; ++i) {
+    const double a = 0.5 * (x[i] + (1.0 - x[n - 1 - i]));
+    x[i] = a;
+    x[n - 1 - i] = 1.0 - a;
+    if (w) {
+      const double b = 0.5 * ((*w)[i] + (*w)[n - 1 - i]);
+      (*w)[i] = b;
+      (*w)[n - 1 - i] = b;
+    }
+  }
+  if (n & 1) x[n / 2] = 0.5;
+}
+
+// Even-odd form of the operator O (dout x din, row-major) at t + off.
+void put_eo(std::vector<double>& t, int off, const std::vector<double>& O, int dout, int din) {
+  const int oh = (dout + 1) / 2, ih = din / 2;
+  for (int q = 0; q < oh; ++q) {
+    for (int i = 0; i < ih; ++i) {
+      const double lo = O[(size_t)q * din + i], hi = O[(size_t)q * din + din - 1 - i];
+      t[off + q * ih + i] = 0.5 * (lo + hi);
+      t[off + oh * ih + q * ih + i] = 0.5 * (lo - hi);
+    }
+    t[off + 2 * oh * ih + q] = (din & 1) ? O[(size_t)q * din + ih] : 0.0;
+  }
+}
+
+std::vector<double> transpose(const std::vector<double>& O, int rows, int cols) {
+  std::vector<double> T((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) T[(size_t)c * rows + r] = O[(size_t)r * cols + c];
+  return T;
+}
+
 std::vector<double> build_tables(int k, int QC, int QV) {
   const int N = k + 1;
   const TableLayout L = make_layout(N, QC, QV);
   std::vector<double> t(L.total, 0.0);
-  const std::vector<double> nodes = lgl(k);
+  std::vector<double> nodes = lgl(k);
+  symmetrize(nodes);
   std::vector<double> xc, wc, xv, wv, xm, wm, V, D, Vg, Dg;
   gauss(QC, xc, wc);
   gauss(QV, xv, wv);
   gauss(N, xm, wm);
-  lagrange(nodes, xc, V, D);
-  std::copy(V.begin(), V.end(), t.begin() + L.Sc);
+  symmetrize(xc, &wc);
+  symmetrize(xv, &wv);
+  symmetrize(xm, &wm);
+  lagrange(nodes, xc, V, D);  // S_c[q][i] = l_i(x_q)
+  put_eo(t, L.eo[EO_SC], V, QC, N);
+  put_eo(t, L.eo[EO_SCT], transpose(V, QC, N), N, QC);
   lagrange(xc, xc, Vg, Dg);  // collocation derivative on the convective Gauss points
-  std::copy(Dg.begin(), Dg.end(), t.begin() + L.Dc);
+  put_eo(t, L.eo[EO_DC], Dg, QC, QC);
+  put_eo(t, L.eo[EO_DCT], transpose(Dg, QC, QC), QC, QC);
   lagrange(nodes, xv, V, D);
-  std::copy(V.begin(), V.end(), t.begin() + L.Sv);
+  put_eo(t, L.eo[EO_SV], V, QV, N);
+  put_eo(t, L.eo[EO_SVT], transpose(V, QV, N), N, QV);
   lagrange(xv, xv, Vg, Dg);
-  std::copy(Dg.begin(), Dg.end(), t.begin() + L.Dv);
-  lagrange(nodes, xm, V, D);
-  std::copy(V.begin(), V.end(), t.begin() + L.Sm);
+  put_eo(t, L.eo[EO_DV], Dg, QV, QV);
+  put_eo(t, L.eo[EO_DVT], transpose(Dg, QV, QV), QV, QV);
+  lagrange(nodes, xm, V, D);  // square LGL-to-Gauss matrix at the k+1 mass points
+  put_eo(t, L.eo[EO_SM], V, N, N);
   if (!invert(V, N)) return {};
-  std::copy(V.begin(), V.end(), t.begin() + L.Smi);
+  put_eo(t, L.eo[EO_SMI], V, N, N);
+  put_eo(t, L.eo[EO_SMIT], transpose(V, N, N), N, N);
   std::copy(wc.begin(), wc.end(), t.begin() + L.wc);
   std::copy(wv.begin(), wv.end(), t.begin() + L.wv);
   std::copy(wm.begin(), wm.end(), t.begin() + L.wm);
@@ -355,6 +401,8 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   kp.lam = c->lam;
   kp.cv = c->cv;
   kp.Tw = c->Tw;
+  kp.rho_ref = prm->rho0;
+  kp.rhoE_ref = prm->rho0 * c->cv * c->Tw;
   kp.tau = c->d_tau;
   kp.conv = kp.visc = 1;
   kp.tables = prm->precision == DGCNS_MIXED ? (const void*)c->d_tab32 : (const void*)c->d_tab64;
@@ -408,7 +456,8 @@ int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {
   if (!xyz) return fail(c, DGCNS_ERR_INVALID_ARG, "xyz is NULL");
   const dgcns_mesh& m = c->mesh;
   const int N = c->N, N3 = c->N3;
-  const std::vector<double> nodes = lgl(c->prm.k);
+  std::vector<double> nodes = lgl(c->prm.k);
+  symmetrize(nodes);
   double h[3];
   for (int d = 0; d < 3; ++d) h[d] = (m.hi[d] - m.lo[d]) / m.n[d];
   std::vector<double> host((size_t)c->Nc * 3 * N3);
