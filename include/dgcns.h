@@ -147,6 +147,28 @@ int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U,
  * (out is still filled). */
 int dg_cns_diagnostics(dgcns_ctx* ctx, const double* U, const void* L_of_U, double* out);
 
+/* Diagnostics without any memory allocation, for callers that may not
+ * allocate while they run: code that owns all device memory through its own
+ * pool, loops with a fixed memory budget, or steps recorded while allocation
+ * is not permitted.  (No counterpart in the paper: an interface addition.)
+ * Computes the same DGCNS_NDIAG values as dg_cns_diagnostics, but writes them
+ * to out_dev, a DEVICE array of DGCNS_NDIAG doubles, asynchronously on the
+ * context's stream: no host copy, no synchronisation, no cudaMalloc/cudaFree.
+ * Scratch: one static device array of DGCNS_NOALLOC_SCRATCH_BYTES (16 MiB)
+ * that every GPU loading this library holds until the process exits.  It
+ * holds DGCNS_NOALLOC_SCRATCH_BYTES / 80 = 209715 partial-sum rows, one per
+ * batch of 2 cells (1 cell when nq_conv^3 > 300); a mesh needing more rows is
+ * rejected with DGCNS_ERR_INVALID_ARG before anything is launched.  Every row
+ * a call reads it first writes, so nothing needs clearing between calls.  All
+ * calls (all contexts on the device) share that array: calls that may overlap
+ * on the GPU (different streams, no ordering) race and give wrong results.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  A non-finite state is reported in out_dev[8]
+ * only (the call cannot see it without synchronising). */
+#define DGCNS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int dg_cns_diagnostics_noalloc(dgcns_ctx* ctx, const double* U, const void* L_of_U, double* out_dev);
+
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int dg_cns_launch_count(const dgcns_ctx* ctx, int64_t* count);
 

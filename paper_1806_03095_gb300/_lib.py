@@ -17,11 +17,12 @@ KERNEL_SPLIT, KERNEL_FUSED = 0, 1
 MAP_AFFINE, MAP_CHANNEL, MAP_SINE = 0, 1, 2
 OP_L, OP_F, OP_FC, OP_FV = 0, 1, 2, 3
 NDIAG = 9
+NOALLOC_SCRATCH_BYTES = 16 << 20  # static device scratch of dg_cns_diagnostics_noalloc
 
 # Every symbol include/dgcns.h declares.
 EXPORTS = ("dg_cns_create", "dg_cns_destroy", "dg_cns_set_stream", "dg_cns_sizes", "dg_cns_node_coords",
            "dg_cns_apply", "dg_cns_inverse_mass", "dg_cns_rk_stage", "dg_cns_rk_steps", "dg_cns_diagnostics",
-           "dg_cns_launch_count", "dg_cns_last_error")
+           "dg_cns_diagnostics_noalloc", "dg_cns_launch_count", "dg_cns_last_error")
 
 
 class Mesh(ctypes.Structure):
@@ -63,6 +64,7 @@ def load(path=LIB_PATH):
         "dg_cns_rk_stage": ([vp, ci, cd, cd, vp, vp, vp], ci),
         "dg_cns_rk_steps": ([vp, ci, cd, cd, vp, vp, vp], ci),
         "dg_cns_diagnostics": ([vp, vp, vp, dp], ci),
+        "dg_cns_diagnostics_noalloc": ([vp, vp, vp, vp], ci),
         "dg_cns_launch_count": ([vp, i64p], ci),
         "dg_cns_last_error": ([vp], ctypes.c_char_p),
     }

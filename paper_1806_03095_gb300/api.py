@@ -134,6 +134,21 @@ class DGCNS:
             self._check(rc)
         return np.array(out[:], dtype=np.float64)
 
+    def dg_cns_diagnostics_noalloc(self, U, LU=None, out=None):
+        """Diagnostics into a device tensor of NDIAG doubles, allocating nothing in the
+        library (its scratch is a fixed static device array; see include/dgcns.h).
+        Asynchronous: the values are valid once torch's current stream reaches them."""
+        self._state(U, "U")
+        if LU is not None:
+            self._state(LU, "L_of_U", self.rdtype)
+        if out is None:
+            out = torch.empty(NDIAG, dtype=torch.float64, device=self.device)
+        elif out.device != self.device or out.dtype != torch.float64 or out.numel() < NDIAG or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 device tensor with at least %d entries" % NDIAG)
+        self._sync_stream()
+        self._check(self.lib.dg_cns_diagnostics_noalloc(self.ctx, _ptr(U), _ptr(LU), _ptr(out)))
+        return out
+
     def dg_cns_launch_count(self):
         c = ctypes.c_int64()
         self._check(self.lib.dg_cns_launch_count(self.ctx, ctypes.byref(c)))

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -591,6 +592,82 @@ int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* ou
   for (int a = 0; a < 5; ++a) out[3 + a] = acc[4 + a];
   out[8] = acc[9];
   return acc[9] > 0 ? fail(c, DGCNS_ERR_NONFINITE, "state has non-finite entries") : DGCNS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics without allocation: the per-block partial sums live in a static
+// device array instead of the context's buffer, and the final reduction runs
+// on the GPU into the caller's device output.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+constexpr int kNoallocRows = (int)(DGCNS_NOALLOC_SCRATCH_BYTES / (10 * sizeof(double)));
+static __device__ __align__(256) double g_noalloc_partials[(size_t)kNoallocRows * 10];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of g_noalloc_partials on the current device (looked up once per device).
+int noalloc_scratch(dgcns_ctx* c, double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return cuda_fail(c, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p)
+      return fail(c, DGCNS_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") +
+                                         cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return DGCNS_OK;
+}
+
+// Sum the partial rows in order (the same order as the host reduction of
+// dg_cns_diagnostics) and write the normalised diagnostics.
+__global__ void noalloc_finalize(const double* __restrict__ partial, int nrows, double nu, int has_L,
+                                 double* __restrict__ out) {
+  __shared__ double acc[10];
+  if (threadIdx.x < 10) {
+    double s = 0.0;
+    for (int b = 0; b < nrows; ++b) s += partial[(size_t)b * 10 + threadIdx.x];
+    acc[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = acc[1] / acc[0];
+    out[1] = nu * acc[2] / acc[0];
+    out[2] = has_L ? -acc[3] / acc[0] : 0.0;
+    for (int a = 0; a < 5; ++a) out[3 + a] = acc[4 + a];
+    out[8] = acc[9];
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, double* out_dev) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U || !out_dev) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  KParams kp = c->kp;
+  kp.tables = c->d_tab64;
+  const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
+  int nblk = 0;
+  if (f(kp, nullptr, nullptr, nullptr, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics set-up");
+  if (nblk > kNoallocRows)
+    return fail(c, DGCNS_ERR_INVALID_ARG,
+                "mesh too large for the no-alloc diagnostics: it needs " + std::to_string(nblk) +
+                    " partial rows, the static scratch holds " + std::to_string(kNoallocRows));
+  double* scratch = nullptr;
+  const int r = noalloc_scratch(c, &scratch);
+  if (r) return r;
+  if (f(kp, U, LU, scratch, &nblk, c->stream) != 0) return cuda_fail(c, "no-alloc diagnostics kernel launch");
+  noalloc_finalize<<<1, 32, 0, c->stream>>>(scratch, nblk, c->nu, LU ? 1 : 0, out_dev);
+  c->launches += 2;
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, "no-alloc diagnostics finalize launch");
+  return DGCNS_OK;
 }
 
 int dg_cns_launch_count(const dgcns_ctx* c, int64_t* count) {
