@@ -16,11 +16,18 @@ def tgv(N, k, precision=0, kernel=1):
                 kernel=kernel, u_max=1.0, h_min=2 * PI / N, Cr=0.4, D=0.02)
 
 
+def channel_h_min(N, C=1.8):
+    """Minimum vertex distance of the stretched channel grid: the wall-adjacent cell height."""
+    y0 = math.tanh(C * (2.0 * 0.0 - 1.0)) / math.tanh(C)
+    y1 = math.tanh(C * (2.0 * (1.0 / N) - 1.0)) / math.tanh(C)
+    return min(y1 - y0, 2 * PI / N, PI / N)
+
+
 def channel(N=32, k=3, precision=1, kernel=1, mapping=1):
     return dict(name="channel%d_k%d" % (N, k), ncells=(N, N, N), lo=(0.0, -1.0, 0.0), hi=(2 * PI, 1.0, PI),
                 periodic=(1, 0, 1), k=k, nq_conv=(3 * k) // 2 + 1, nq_visc=k + 1, Re=180.0, Ma=0.1, Pr=0.71,
                 gamma=1.4, R=287.0, u_mach=18.3, body_force=(1.0, 0.0, 0.0), mapping=mapping, map_param=1.8,
-                precision=precision, kernel=kernel, u_max=18.3, h_min=None, Cr=0.4, D=0.02)
+                precision=precision, kernel=kernel, u_max=18.3, h_min=channel_h_min(N), Cr=0.4, D=0.02)
 
 
 WORKLOADS = {

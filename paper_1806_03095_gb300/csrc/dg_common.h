@@ -13,7 +13,7 @@ namespace dgcns {
 // decomposition): for q < ceil(DOUT/2), i < floor(DIN/2)
 //   a[q][i] = (O[q][i] + O[q][DIN-1-i]) / 2,  b[q][i] = (O[q][i] - O[q][DIN-1-i]) / 2,
 //   c[q]    = O[q][DIN/2] (middle column, DIN odd; else 0).
-enum EoOp { EO_SC, EO_SCT, EO_DC, EO_DCT, EO_SV, EO_SVT, EO_DV, EO_DVT, EO_SMI, EO_SMIT, EO_SM, EO_NOPS };
+enum EoOp { EO_SC, EO_SCT, EO_DC, EO_DCT, EO_SV, EO_SVT, EO_DV, EO_DVT, EO_SMI, EO_SMIT, EO_SM, EO_DM, EO_NOPS };
 
 constexpr int eo_size(int dout, int din) { return ((dout + 1) / 2) * (din / 2) * 2 + (dout + 1) / 2; }
 
@@ -32,7 +32,7 @@ constexpr TableLayout make_layout(int N, int QC, int QV) {
   L.QV = QV;
   int o = 0;
   const int dims[EO_NOPS][2] = {{QC, N}, {N, QC}, {QC, QC}, {QC, QC}, {QV, N}, {N, QV},
-                                {QV, QV}, {QV, QV}, {N, N},   {N, N},   {N, N}};
+                                {QV, QV}, {QV, QV}, {N, N},   {N, N},   {N, N},  {N, N}};
   for (int k = 0; k < EO_NOPS; ++k) {
     L.eo[k] = o;
     o += eo_size(dims[k][0], dims[k][1]);
@@ -63,6 +63,14 @@ struct KParams {
   double A, B, dt;      // 2N stage coefficients (out_mode 2)
   const double* tau;    // [Nc] penalty per cell (FP64)
   const void* tables;   // device tables of the kernel's precision
+  // Stored geometry (non-affine meshes), in the kernel's precision (quadrature weights excluded):
+  //   gcc [Nc][10][QC^3], gcv [Nc][10][QV^3]: J^{-1}[b][a] (index 3b+a) and |det J| at cell points;
+  //   gfc [Nc][6][13][QC^2], gfv [Nc][6][13][QV^2]: J^{-1} (9), unit outward normal n (3) and the
+  //   area element dA = |det J| |J^{-T} n_xi| (1), face f = 2d + s;  gm [Nc][N^3]: |det J| at
+  //   the k+1 mass points.
+  const void *gcc, *gcv, *gfc, *gfv, *gm;
 };
+
+constexpr int GEO_AFFINE = 0, GEO_STORED = 1;
 
 }  // namespace dgcns

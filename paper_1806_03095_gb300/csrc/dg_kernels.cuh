@@ -27,7 +27,7 @@ namespace dgcns {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Tab {
-  const T *eSc, *eScT, *eDc, *eDcT, *eSv, *eSvT, *eDv, *eDvT, *eSmi, *eSmiT, *eSm;
+  const T *eSc, *eScT, *eDc, *eDcT, *eSv, *eSvT, *eDv, *eDvT, *eSmi, *eSmiT, *eSm, *eDm;
   const T *wc, *wv, *wm, *dl0, *dl1;
 };
 
@@ -38,7 +38,7 @@ __device__ __forceinline__ Tab<T> load_tables(const T* __restrict__ g, T* s) {
   Tab<T> t;
   t.eSc = s + L.eo[EO_SC]; t.eScT = s + L.eo[EO_SCT]; t.eDc = s + L.eo[EO_DC]; t.eDcT = s + L.eo[EO_DCT];
   t.eSv = s + L.eo[EO_SV]; t.eSvT = s + L.eo[EO_SVT]; t.eDv = s + L.eo[EO_DV]; t.eDvT = s + L.eo[EO_DVT];
-  t.eSmi = s + L.eo[EO_SMI]; t.eSmiT = s + L.eo[EO_SMIT]; t.eSm = s + L.eo[EO_SM];
+  t.eSmi = s + L.eo[EO_SMI]; t.eSmiT = s + L.eo[EO_SMIT]; t.eSm = s + L.eo[EO_SM]; t.eDm = s + L.eo[EO_DM];
   t.wc = s + L.wc; t.wv = s + L.wv; t.wm = s + L.wm; t.dl0 = s + L.dl0; t.dl1 = s + L.dl1;
   return t;
 }
@@ -235,9 +235,9 @@ struct Sizes {
 // su, sr: [CB][5][N^3]; ar: arena of CB*CELL_ARENA elements.
 // Affine geometry: J = diag(h), |J| = h0 h1 h2.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB>
+template <typename T, int N, int QC, int QV, int CB, int GEO>
 __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph,
-                           int nb) {
+                           int e0, int nb) {
   const T h[3] = {T(kp.h[0]), T(kp.h[1]), T(kp.h[2])};
   const T detJ = h[0] * h[1] * h[2];
   const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
@@ -266,13 +266,30 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       const T rinv = T(1) / (ph.rho_r + u[0]);
       const T dp = pressure_dev(u, rinv, ph.gm1);
       T* Fd[3] = {F0, F1, F2};
+      if (GEO == GEO_AFFINE) {
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        T f[5];
-        conv_flux_dir(u, rinv, dp, ph.H_r, j, f);
-        const T s = -w * hinv[j];
+        for (int j = 0; j < 3; ++j) {
+          T f[5];
+          conv_flux_dir(u, rinv, dp, ph.H_r, j, f);
+          const T s = -w * hinv[j];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) Fd[j][(e * 5 + c) * P + p] = s * f[c];
+          for (int c = 0; c < 5; ++c) Fd[j][(e * 5 + c) * P + p] = s * f[c];
+        }
+      } else {
+        // contravariant flux Ft_b = -|J| w sum_a J^{-1}[b][a] F[.][a]
+        const T* g = static_cast<const T*>(kp.gcc) + (size_t)(e0 + e) * 10 * P + p;
+        T Ji[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) Ji[m] = g[m * P];
+        const T jw = -g[9 * P] * tb.wc[q0] * tb.wc[q1] * tb.wc[q2];
+        T F[3][5];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) conv_flux_dir(u, rinv, dp, ph.H_r, a, F[a]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 5; ++c)
+            Fd[b][(e * 5 + c) * P + p] = jw * (Ji[3 * b] * F[0][c] + Ji[3 * b + 1] * F[1][c] + Ji[3 * b + 2] * F[2][c]);
       }
     }
     __syncthreads();
@@ -314,18 +331,39 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       const T w = tb.wv[q0] * tb.wv[q1] * tb.wv[q2] * detJ;
       T u[5], G[5][3], F[5][3];
       T* Vd[3] = {V1, V2, V3};
+      if (GEO == GEO_AFFINE) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        u[c] = V0[(e * 5 + c) * P + p];
+        for (int c = 0; c < 5; ++c) {
+          u[c] = V0[(e * 5 + c) * P + p];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) G[c][j] = Vd[j][(e * 5 + c) * P + p] * hinv[j];
-      }
-      visc_flux(u, G, ph, F);
+          for (int j = 0; j < 3; ++j) G[c][j] = Vd[j][(e * 5 + c) * P + p] * hinv[j];
+        }
+        visc_flux(u, G, ph, F);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const T s = w * hinv[j];
+        for (int j = 0; j < 3; ++j) {
+          const T s = w * hinv[j];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) Vd[j][(e * 5 + c) * P + p] = s * F[c][j];
+          for (int c = 0; c < 5; ++c) Vd[j][(e * 5 + c) * P + p] = s * F[c][j];
+        }
+      } else {
+        const T* g = static_cast<const T*>(kp.gcv) + (size_t)(e0 + e) * 10 * P + p;
+        T Ji[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) Ji[m] = g[m * P];
+        const T jw = g[9 * P] * tb.wv[q0] * tb.wv[q1] * tb.wv[q2];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          u[c] = V0[(e * 5 + c) * P + p];
+          const T g0 = Vd[0][(e * 5 + c) * P + p], g1 = Vd[1][(e * 5 + c) * P + p], g2 = Vd[2][(e * 5 + c) * P + p];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) G[c][a] = Ji[a] * g0 + Ji[3 + a] * g1 + Ji[6 + a] * g2;
+        }
+        visc_flux(u, G, ph, F);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 5; ++c)
+            Vd[b][(e * 5 + c) * P + p] = jw * (Ji[3 * b] * F[c][0] + Ji[3 * b + 1] * F[c][1] + Ji[3 * b + 2] * F[c][2]);
       }
     }
     __syncthreads();
@@ -353,9 +391,10 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
 // su: own nodal state, sn: neighbour nodal state (unused where wall[e]),
 // tau_f[e]: face penalty, sr: accumulated residual, fa: face arena.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, int d>
-__device__ void face_terms(const T* su, const T* sn, const int* wall, const T* tau_f, T* sr, T* fa,
-                           const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int nb, int s) {
+template <typename T, int N, int QC, int QV, int CB, int d, int GEO>
+__device__ void face_terms(const T* su, const T* sn, const int* wall, const int* nbi, const T* tau_f, T* sr, T* fa,
+                           const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int e0, int nb, int s) {
+  const int f = 2 * d + s, fo = 2 * d + (1 - s);  // own face, neighbour's face
   constexpr int N2 = N * N, N3 = N * N * N;
   constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   const T hinv[3] = {T(1.0 / kp.h[0]), T(1.0 / kp.h[1]), T(1.0 / kp.h[2])};
@@ -402,12 +441,32 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
       const T lm = sqrt(um[1] * um[1] + um[2] * um[2] + um[3] * um[3]) * rm + sqrt(fabs(ph.gamma * (ph.p_r + pm) * rm));
       const T lp = sqrt(up[1] * up[1] + up[2] * up[2] + up[3] * up[3]) * rp + sqrt(fabs(ph.gamma * (ph.p_r + pp) * rp));
       const T lam = lm > lp ? lm : lp;
-      T fm[5], fp[5];
-      conv_flux_dir(um, rm, pm, ph.H_r, d, fm);
-      conv_flux_dir(up, rp, pp, ph.H_r, d, fp);
+      if (GEO == GEO_AFFINE) {
+        T fm[5], fp[5];
+        conv_flux_dir(um, rm, pm, ph.H_r, d, fm);
+        conv_flux_dir(up, rp, pp, ph.H_r, d, fp);
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        Um[(e * 5 + c) * P + p] = w * (T(0.5) * sgn * (fm[c] + fp[c]) + T(0.5) * lam * (um[c] - up[c]));
+        for (int c = 0; c < 5; ++c)
+          Um[(e * 5 + c) * P + p] = w * (T(0.5) * sgn * (fm[c] + fp[c]) + T(0.5) * lam * (um[c] - up[c]));
+      } else {
+        const T* g = static_cast<const T*>(kp.gfc) + ((size_t)(e0 + e) * 6 + f) * 13 * P + p;
+        const T n0 = g[9 * P], n1 = g[10 * P], n2 = g[11 * P];
+        const T dw = g[12 * P] * tb.wc[p % QC] * tb.wc[p / QC];
+        T fn[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fn[c] = T(0);
+        const T nn[3] = {n0, n1, n2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          T fm[5], fp[5];
+          conv_flux_dir(um, rm, pm, ph.H_r, a, fm);
+          conv_flux_dir(up, rp, pp, ph.H_r, a, fp);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) fn[c] += (fm[c] + fp[c]) * nn[a];
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Um[(e * 5 + c) * P + p] = dw * (T(0.5) * fn[c] + T(0.5) * lam * (um[c] - up[c]));
+      }
     }
     __syncthreads();
     sweep<T, 1, QC, QC, 1, N, 1, false>(Um, Tm, tb.eScT, nbl);
@@ -485,16 +544,52 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
       const T w = tb.wv[p % QV] * tb.wv[p / QV] * area;
       const int o = e * 5 * P + p;
       T um[5], up[5], Gm[5][3], Gp[5][3];
+      T nrm[3] = {T(0), T(0), T(0)};
+      T Jm[9];
+      T wgt = w;
+      if (GEO == GEO_AFFINE) {
+        nrm[d] = sgn;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        um[c] = Um[o + c * P];
-        up[c] = Up[o + c * P];
-        Gm[c][t1] = G1m[o + c * P] * hinv[t1];
-        Gm[c][t2] = G2m[o + c * P] * hinv[t2];
-        Gm[c][d] = Gdm[o + c * P] * hinv[d];
-        Gp[c][t1] = G1p[o + c * P] * hinv[t1];
-        Gp[c][t2] = G2p[o + c * P] * hinv[t2];
-        Gp[c][d] = Gdp[o + c * P] * hinv[d];
+        for (int c = 0; c < 5; ++c) {
+          um[c] = Um[o + c * P];
+          up[c] = Up[o + c * P];
+          Gm[c][t1] = G1m[o + c * P] * hinv[t1];
+          Gm[c][t2] = G2m[o + c * P] * hinv[t2];
+          Gm[c][d] = Gdm[o + c * P] * hinv[d];
+          Gp[c][t1] = G1p[o + c * P] * hinv[t1];
+          Gp[c][t2] = G2p[o + c * P] * hinv[t2];
+          Gp[c][d] = Gdp[o + c * P] * hinv[d];
+        }
+      } else {
+        // reference derivative directions: t1, t2, d  ->  physical G[c][a] = sum_b J^{-1}[b][a] g_b
+        const T* g = static_cast<const T*>(kp.gfv) + ((size_t)(e0 + e) * 6 + f) * 13 * P + p;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) Jm[m] = g[m * P];
+        nrm[0] = g[9 * P];
+        nrm[1] = g[10 * P];
+        nrm[2] = g[11 * P];
+        wgt = g[12 * P] * tb.wv[p % QV] * tb.wv[p / QV];
+        T Jp[9];
+        if (!wall[e]) {
+          const T* gp = static_cast<const T*>(kp.gfv) + ((size_t)nbi[e] * 6 + fo) * 13 * P + p;
+#pragma unroll
+          for (int m = 0; m < 9; ++m) Jp[m] = gp[m * P];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 9; ++m) Jp[m] = Jm[m];
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          um[c] = Um[o + c * P];
+          up[c] = Up[o + c * P];
+          const T a1 = G1m[o + c * P], a2 = G2m[o + c * P], ad = Gdm[o + c * P];
+          const T b1 = G1p[o + c * P], b2 = G2p[o + c * P], bd = Gdp[o + c * P];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            Gm[c][a] = Jm[3 * t1 + a] * a1 + Jm[3 * t2 + a] * a2 + Jm[3 * d + a] * ad;
+            Gp[c][a] = Jp[3 * t1 + a] * b1 + Jp[3 * t2 + a] * b2 + Jp[3 * d + a] * bd;
+          }
+        }
       }
       if (wall[e]) {
         wall_ghost(um, ph, up);
@@ -512,24 +607,31 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
       for (int c = 0; c < 5; ++c) {
         jmp[c] = um[c] - up[c];
         // -(V, Q*.n):  Q*.n = {{F_v}}.n - tau (U- - U+)
-        Um[o + c * P] = -w * (T(0.5) * sgn * (Fm[c][d] + Fp[c][d]) - tau * jmp[c]);
+        const T fvn = (Fm[c][0] + Fp[c][0]) * nrm[0] + (Fm[c][1] + Fp[c][1]) * nrm[1] + (Fm[c][2] + Fp[c][2]) * nrm[2];
+        Um[o + c * P] = -wgt * (T(0.5) * fvn - tau * jmp[c]);
       }
       // -1/2 (grad V, F_v(U-, [[U]])) with [[U]] = (U- - U+) (x) n
       T Jg[5][3];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        Jg[c][0] = T(0);
-        Jg[c][1] = T(0);
-        Jg[c][2] = T(0);
-        Jg[c][d] = sgn * jmp[c];
-      }
-      visc_flux(um, Jg, ph, Fm);
-      const T hw = T(-0.5) * w;
+      for (int c = 0; c < 5; ++c)
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        G1m[o + c * P] = hw * hinv[t1] * Fm[c][t1];
-        G2m[o + c * P] = hw * hinv[t2] * Fm[c][t2];
-        Gdm[o + c * P] = hw * hinv[d] * Fm[c][d];
+        for (int a = 0; a < 3; ++a) Jg[c][a] = jmp[c] * nrm[a];
+      visc_flux(um, Jg, ph, Fm);
+      const T hw = T(-0.5) * wgt;
+      if (GEO == GEO_AFFINE) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          G1m[o + c * P] = hw * hinv[t1] * Fm[c][t1];
+          G2m[o + c * P] = hw * hinv[t2] * Fm[c][t2];
+          Gdm[o + c * P] = hw * hinv[d] * Fm[c][d];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          G1m[o + c * P] = hw * (Jm[3 * t1] * Fm[c][0] + Jm[3 * t1 + 1] * Fm[c][1] + Jm[3 * t1 + 2] * Fm[c][2]);
+          G2m[o + c * P] = hw * (Jm[3 * t2] * Fm[c][0] + Jm[3 * t2 + 1] * Fm[c][1] + Jm[3 * t2 + 2] * Fm[c][2]);
+          Gdm[o + c * P] = hw * (Jm[3 * d] * Fm[c][0] + Jm[3 * d + 1] * Fm[c][1] + Jm[3 * d + 2] * Fm[c][2]);
+        }
       }
     }
     __syncthreads();
@@ -570,9 +672,9 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const T* t
 // S^{-1} F_rhs(x_q) (nodal coefficients of its Gauss-point interpolant).
 // su is needed only for the body force (u at the mass points).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int CB>
-__device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int nb, bool negate,
-                             bool add_force) {
+template <typename T, int N, int CB, int GEO>
+__device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int e0, int nb,
+                             bool negate, bool add_force) {
   constexpr int N3 = N * N * N;
   const int nbl = nb * 5;
   T* A = ma;
@@ -587,7 +689,12 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
   const T sg = negate ? T(-1) : T(1);
   for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
     const int p = idx % N3;
-    const T w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] * detJ;
+    T w;
+    if (GEO == GEO_AFFINE)
+      w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] * detJ;
+    else
+      w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] *
+          static_cast<const T*>(kp.gm)[(size_t)(e0 + idx / (5 * N3)) * N3 + p];
     A[idx] *= sg / w;
   }
   __syncthreads();

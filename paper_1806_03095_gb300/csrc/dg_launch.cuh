@@ -43,7 +43,7 @@ __device__ __forceinline__ double ref_of(const KParams& kp, int c) {
 // is read from Rin.  Output (kp.out_mode): 0 write R, 1 write L, 2 RK stage
 // dU <- A dU + dt L, U_out <- U + B dU.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS>
+template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
 __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const double* __restrict__ U,
                                                    const T* Rin, T* Rout, T* dU, double* Uout) {
   using S = Sizes<N, QC, QV>;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
   }
   __syncthreads();
 
-  if (CELL) cell_terms<T, N, QC, QV, CB>(su, sr, ar, tb, kp, ph, nb);
+  if (CELL) cell_terms<T, N, QC, QV, CB, GEO>(su, sr, ar, tb, kp, ph, e0, nb);
 
   if (FACE) {
     for (int d = 0; d < 3; ++d) {
@@ -115,14 +115,15 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
           if (!wall[e]) sn[i] = T(U[(size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3)] - ref_of(kp, (i / N3) % 5));
         }
         __syncthreads();
-        if (d == 0) face_terms<T, N, QC, QV, CB, 0>(su, sn, wall, tau_f, sr, ar, tb, kp, ph, nb, s);
-        if (d == 1) face_terms<T, N, QC, QV, CB, 1>(su, sn, wall, tau_f, sr, ar, tb, kp, ph, nb, s);
-        if (d == 2) face_terms<T, N, QC, QV, CB, 2>(su, sn, wall, tau_f, sr, ar, tb, kp, ph, nb, s);
+        if (d == 0) face_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
+        if (d == 1) face_terms<T, N, QC, QV, CB, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
+        if (d == 2) face_terms<T, N, QC, QV, CB, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
       }
     }
   }
 
-  if (MASS) inverse_mass<T, N, CB>(su, sr, ar, tb, kp, nb, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0);
+  if (MASS)
+    inverse_mass<T, N, CB, GEO>(su, sr, ar, tb, kp, e0, nb, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0);
 
   if (kp.out_mode == 2) {
     const double A = kp.A, B = kp.B, dt = kp.dt;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
 // ---------------------------------------------------------------------------
 constexpr int NACC = 10;
 
-template <typename TL, int N, int QC, int QV, int CB>
+template <typename TL, int N, int QC, int QV, int CB, int GEO>
 __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const double* __restrict__ U,
                                                      const TL* __restrict__ LU, double* __restrict__ partial) {
   constexpr int N3 = N * N * N, P = QC * QC * QC;
@@ -157,6 +158,9 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
   double* V2 = V1 + CB * 5 * P;
   double* L0 = V2 + CB * 5 * P;    // L(U) at the Gauss points
   double* red = L0 + CB * 5 * P;   // [NT][NACC]
+  double* GU = red + NT * NACC;    // [9][CB P] physical velocity gradient (stored geometry only)
+  const double* gcc = static_cast<const double*>(kp.gcc);
+  const double* gmv = static_cast<const double*>(kp.gm);
   const Tab<double> tb = load_tables<double, N, QC, QV>(static_cast<const double*>(kp.tables), stab);
   const int e0 = blockIdx.x * CB;
   const int nb = min(CB, kp.Nc - e0);
@@ -192,7 +196,8 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
     const double hinv[3] = {1.0 / kp.h[0], 1.0 / kp.h[1], 1.0 / kp.h[2]};
     for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
       const int e = idx / P, p = idx - e * P;
-      const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] * detJ;
+      const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] *
+                       (GEO == GEO_AFFINE ? detJ : gcc[((size_t)(e0 + e) * 10 + 9) * P + p]);
       const int o = e * 5 * P + p;
       const double rinv = 1.0 / V0[o];
       const double u[3] = {V0[o + P] * rinv, V0[o + 2 * P] * rinv, V0[o + 3 * P] * rinv};
@@ -205,31 +210,66 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
         acc[3] += s * w;
       }
     }
-    // grad u : grad u, one reference direction at a time (the sum over j separates)
+    if (GEO == GEO_AFFINE) {
+      // grad u : grad u, one reference direction at a time (the sum over j separates)
 #pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-      __syncthreads();
-      if (j == 0) sweep<double, 0, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
-      if (j == 1) sweep<double, 1, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
-      if (j == 2) sweep<double, 2, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+      for (int j = 0; j < 3; ++j) {
+        __syncthreads();
+        if (j == 0) sweep<double, 0, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        if (j == 1) sweep<double, 1, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        if (j == 2) sweep<double, 2, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+          const int e = idx / P, p = idx - e * P;
+          const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] * detJ;
+          const int o = e * 5 * P + p;
+          const double rinv = 1.0 / V0[o];
+          const double gr = V1[o] * hinv[j];
+          double gg = 0.0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const double ui = V0[o + (1 + i) * P] * rinv;
+            const double gui = (V1[o + (1 + i) * P] * hinv[j] - ui * gr) * rinv;
+            gg += gui * gui;
+          }
+          acc[2] += gg * w;
+        }
+      }
+    } else {
+      // physical velocity gradient du_i/dx_a = sum_b J^{-1}[b][a] du_i/dxi_b, accumulated direction by direction
+      for (int idx = threadIdx.x; idx < 9 * nb * P; idx += blockDim.x) GU[idx] = 0.0;
+#pragma unroll 1
+      for (int j = 0; j < 3; ++j) {
+        __syncthreads();
+        if (j == 0) sweep<double, 0, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        if (j == 1) sweep<double, 1, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        if (j == 2) sweep<double, 2, QC, QC, QC, QC, -1, false>(V0, V1, tb.eDc, nbl);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+          const int e = idx / P, p = idx - e * P;
+          const int o = e * 5 * P + p;
+          const double* g = gcc + (size_t)(e0 + e) * 10 * P + p;
+          const double rinv = 1.0 / V0[o];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const double ui = V0[o + (1 + i) * P] * rinv;
+            const double gui = (V1[o + (1 + i) * P] - ui * V1[o]) * rinv;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) GU[(3 * i + a) * nb * P + idx] += g[(3 * j + a) * P] * gui;
+          }
+        }
+      }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
         const int e = idx / P, p = idx - e * P;
-        const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] * detJ;
-        const int o = e * 5 * P + p;
-        const double rinv = 1.0 / V0[o];
-        const double gr = V1[o] * hinv[j];
+        const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] *
+                         gcc[((size_t)(e0 + e) * 10 + 9) * P + p];
         double gg = 0.0;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const double ui = V0[o + (1 + i) * P] * rinv;
-          const double gui = (V1[o + (1 + i) * P] * hinv[j] - ui * gr) * rinv;
-          gg += gui * gui;
-        }
+        for (int m = 0; m < 9; ++m) gg += GU[m * nb * P + idx] * GU[m * nb * P + idx];
         acc[2] += gg * w;
       }
     }
-    __syncthreads();
     // conservation totals with the k+1 point rule: int U = sum_q U(x_q) |J| w_q
     sweep<double, 0, N, N, N, N, 1, false>(su, V1, tb.eSm, nbl);
     __syncthreads();
@@ -239,7 +279,8 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
     __syncthreads();
     for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
       const int c = (idx / N3) % 5, p = idx % N3;
-      const double w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] * detJ;
+      const double w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] *
+                       (GEO == GEO_AFFINE ? detJ : gmv[(size_t)(e0 + idx / (5 * N3)) * N3 + p]);
       acc[4 + c] += V1[idx] * w;
     }
   }
@@ -255,19 +296,234 @@ __global__ void __launch_bounds__(NT) dg_diag_kernel(const KParams kp, const dou
   }
 }
 
-template <int N, int QC, int QV, int CB>
+template <int N, int QC, int QV, int CB, int GEO>
 constexpr size_t diag_smem_bytes() {
   constexpr int N3 = N * N * N, P = QC * QC * QC;
-  return (table_elems<N, QC, QV>() + 2 * CB * 5 * N3 + 4 * CB * 5 * P + NT * NACC) * sizeof(double) + 64;
+  return (table_elems<N, QC, QV>() + 2 * CB * 5 * N3 + 4 * CB * 5 * P + NT * NACC + (GEO ? 9 * CB * P : 0)) *
+             sizeof(double) + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry precomputation in FP64 (non-affine meshes), one CTA per cell: the
+// Jacobian of the isoparametric map x(xi) = sum_i x_i phi_i(xi) at every point
+// set by interpolation of the node coordinates and collocation derivatives
+// (exact: x is of degree k, the point sets have >= k+1 points), its inverse
+// and determinant; on faces the unit outward normal n = J^{-T} n_xi / |J^{-T} n_xi|
+// and dA = |det J| |J^{-T} n_xi| (Eq. IntegralsReferenceSpace); the penalty
+// tau_e = nu (k+1)^2 (A_interior / 2 + A_boundary) / V with areas and volume
+// as Gauss sums at the convective points (Eq. TauIP_Element).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double inv3(const double J[3][3], double Ji[9]) {
+  // Ji[3b + a] = (J^{-1})[b][a], J[a][b] = d x_a / d xi_b
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const double id = 1.0 / det;
+  Ji[0] = c00 * id;
+  Ji[1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[3] = c01 * id;
+  Ji[4] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[5] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[6] = c02 * id;
+  Ji[7] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[8] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+// Cell points of one point set (Q points per direction, matrices eS: N->Q, eD: Q->Q collocation).
+template <int N, int Q>
+__device__ void geom_cell(const double* X, double* buf, const double* eS, const double* eD, const double* w1,
+                          double* g, double* vol) {
+  constexpr int P = Q * Q * Q;
+  double* A = buf;            // [3][P]
+  double* B = A + 3 * P;
+  double* Xq = B + 3 * P;
+  double* J0 = Xq + 3 * P;
+  double* J1 = J0 + 3 * P;
+  double* J2 = J1 + 3 * P;
+  sweep<double, 0, N, N, N, Q, 1, false>(X, A, eS, 3);
+  __syncthreads();
+  sweep<double, 1, Q, N, N, Q, 1, false>(A, B, eS, 3);
+  __syncthreads();
+  sweep<double, 2, Q, Q, N, Q, 1, false>(B, Xq, eS, 3);
+  __syncthreads();
+  sweep<double, 0, Q, Q, Q, Q, -1, false>(Xq, J0, eD, 3);
+  sweep<double, 1, Q, Q, Q, Q, -1, false>(Xq, J1, eD, 3);
+  sweep<double, 2, Q, Q, Q, Q, -1, false>(Xq, J2, eD, 3);
+  __syncthreads();
+  double v = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double J[3][3], Ji[9];
+    for (int a = 0; a < 3; ++a) {
+      J[a][0] = J0[a * P + p];
+      J[a][1] = J1[a * P + p];
+      J[a][2] = J2[a * P + p];
+    }
+    const double det = fabs(inv3(J, Ji));
+    for (int m = 0; m < 9; ++m) g[m * P + p] = Ji[m];
+    g[9 * P + p] = det;
+    v += det * w1[p % Q] * w1[(p / Q) % Q] * w1[p / (Q * Q)];
+  }
+  if (vol) atomicAdd(vol, v);
+  __syncthreads();
+}
+
+// Face points of face (d, s) for one point set; returns the face area (Gauss sum) via *area.
+template <int N, int Q, int d>
+__device__ void geom_face(const double* X, double* buf, const double* eS, const double* eD, const double* w1,
+                          const double* dl, int s, double* g, double* area) {
+  constexpr int P = Q * Q, N2 = N * N, N3 = N * N * N;
+  constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  double* L = buf;        // [3][N2] face layer
+  double* Dn = L + 3 * N2;  // [3][N2] normal derivative layer
+  double* Tm = Dn + 3 * N2; // [3][N Q]
+  double* Xf = Tm + 3 * N * Q;
+  double* Jt1 = Xf + 3 * P;
+  double* Jt2 = Jt1 + 3 * P;
+  double* Jd = Jt2 + 3 * P;
+  const int id = s ? N - 1 : 0;
+  for (int idx = threadIdx.x; idx < 3 * N2; idx += blockDim.x) {
+    const int a = idx / N2, j = idx % N2;
+    const double* x = X + a * N3;
+    L[idx] = x[face_node<N>(d, id, j % N, j / N)];
+    double dn = 0.0;
+    for (int i = 0; i < N; ++i) dn += dl[i] * x[face_node<N>(d, i, j % N, j / N)];
+    Dn[idx] = dn;
+  }
+  __syncthreads();
+  sweep<double, 0, N, N, 1, Q, 1, false>(L, Tm, eS, 3);
+  __syncthreads();
+  sweep<double, 1, Q, N, 1, Q, 1, false>(Tm, Xf, eS, 3);
+  __syncthreads();
+  sweep<double, 0, N, N, 1, Q, 1, false>(Dn, Tm, eS, 3);
+  __syncthreads();
+  sweep<double, 1, Q, N, 1, Q, 1, false>(Tm, Jd, eS, 3);
+  sweep<double, 0, Q, Q, 1, Q, -1, false>(Xf, Jt1, eD, 3);
+  sweep<double, 1, Q, Q, 1, Q, -1, false>(Xf, Jt2, eD, 3);
+  __syncthreads();
+  const double sgn = s ? 1.0 : -1.0;
+  double ar = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double J[3][3], Ji[9];
+    for (int a = 0; a < 3; ++a) {
+      J[a][t1] = Jt1[a * P + p];
+      J[a][t2] = Jt2[a * P + p];
+      J[a][d] = Jd[a * P + p];
+    }
+    const double det = fabs(inv3(J, Ji));
+    const double v0 = sgn * Ji[3 * d], v1 = sgn * Ji[3 * d + 1], v2 = sgn * Ji[3 * d + 2];
+    const double nv = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    for (int m = 0; m < 9; ++m) g[m * P + p] = Ji[m];
+    g[9 * P + p] = v0 / nv;
+    g[10 * P + p] = v1 / nv;
+    g[11 * P + p] = v2 / nv;
+    g[12 * P + p] = det * nv;
+    ar += det * nv * w1[p % Q] * w1[p / Q];
+  }
+  if (area) atomicAdd(area, ar);
+  __syncthreads();
+}
+
+template <int N, int QC, int QV>
+constexpr int geom_buf_elems() {
+  constexpr int Q = QC > QV ? QC : QV;
+  constexpr int cell = 6 * 3 * Q * Q * Q;
+  constexpr int face = 6 * N * N + 3 * N * Q + 4 * 3 * Q * Q;
+  return (cell > face ? cell : face) > 6 * 3 * N * N * N ? (cell > face ? cell : face) : 6 * 3 * N * N * N;
+}
+
+template <int N, int QC, int QV>
+__global__ void __launch_bounds__(NT) dg_geom_kernel(const KParams kp, const double* __restrict__ xyz,
+                                                     double* gcc, double* gcv, double* gfc, double* gfv, double* gm,
+                                                     double* tau, double nu_kk) {
+  constexpr int N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* stab = sm;
+  double* X = stab + table_elems<N, QC, QV>();
+  double* buf = X + 3 * N3;
+  double* red = buf + geom_buf_elems<N, QC, QV>();  // [0] volume, [1] interior area, [2] boundary area, [3] face tmp
+  const Tab<double> tb = load_tables<double, N, QC, QV>(static_cast<const double*>(kp.tables), stab);
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) X[i] = xyz[(size_t)e * 3 * N3 + i];
+  if (threadIdx.x < 4) red[threadIdx.x] = 0.0;
+  __syncthreads();
+  geom_cell<N, QC>(X, buf, tb.eSc, tb.eDc, tb.wc, gcc + (size_t)e * 10 * QC * QC * QC, red);
+  geom_cell<N, QV>(X, buf, tb.eSv, tb.eDv, tb.wv, gcv + (size_t)e * 10 * QV * QV * QV, nullptr);
+  {
+    // |det J| at the k+1 mass points
+    double* A = buf;
+    double* B = A + 3 * N3;
+    double* Xq = B + 3 * N3;
+    double* J0 = Xq + 3 * N3;
+    double* J1 = J0 + 3 * N3;
+    double* J2 = J1 + 3 * N3;
+    sweep<double, 0, N, N, N, N, 1, false>(X, A, tb.eSm, 3);
+    __syncthreads();
+    sweep<double, 1, N, N, N, N, 1, false>(A, B, tb.eSm, 3);
+    __syncthreads();
+    sweep<double, 2, N, N, N, N, 1, false>(B, Xq, tb.eSm, 3);
+    __syncthreads();
+    sweep<double, 0, N, N, N, N, -1, false>(Xq, J0, tb.eDm, 3);
+    sweep<double, 1, N, N, N, N, -1, false>(Xq, J1, tb.eDm, 3);
+    sweep<double, 2, N, N, N, N, -1, false>(Xq, J2, tb.eDm, 3);
+    __syncthreads();
+    for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+      double J[3][3], Ji[9];
+      for (int a = 0; a < 3; ++a) {
+        J[a][0] = J0[a * N3 + p];
+        J[a][1] = J1[a * N3 + p];
+        J[a][2] = J2[a * N3 + p];
+      }
+      gm[(size_t)e * N3 + p] = fabs(inv3(J, Ji));
+    }
+    __syncthreads();
+  }
+  const int cc[3] = {e % kp.nc[0], (e / kp.nc[0]) % kp.nc[1], e / (kp.nc[0] * kp.nc[1])};
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * d + s;
+      const double* dl = s ? tb.dl1 : tb.dl0;
+      double* gc = gfc + ((size_t)e * 6 + f) * 13 * QC * QC;
+      double* gv = gfv + ((size_t)e * 6 + f) * 13 * QV * QV;
+      if (threadIdx.x == 0) red[3] = 0.0;
+      __syncthreads();
+      if (d == 0) { geom_face<N, QC, 0>(X, buf, tb.eSc, tb.eDc, tb.wc, dl, s, gc, red + 3); geom_face<N, QV, 0>(X, buf, tb.eSv, tb.eDv, tb.wv, dl, s, gv, nullptr); }
+      if (d == 1) { geom_face<N, QC, 1>(X, buf, tb.eSc, tb.eDc, tb.wc, dl, s, gc, red + 3); geom_face<N, QV, 1>(X, buf, tb.eSv, tb.eDv, tb.wv, dl, s, gv, nullptr); }
+      if (d == 2) { geom_face<N, QC, 2>(X, buf, tb.eSc, tb.eDc, tb.wc, dl, s, gc, red + 3); geom_face<N, QV, 2>(X, buf, tb.eSv, tb.eDv, tb.wv, dl, s, gv, nullptr); }
+      if (threadIdx.x == 0) {
+        const bool boundary = !kp.periodic[d] && ((s == 0 && cc[d] == 0) || (s == 1 && cc[d] == kp.nc[d] - 1));
+        red[boundary ? 2 : 1] += red[3];
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) tau[e] = nu_kk * (0.5 * red[1] + red[2]) / red[0];
+}
+
+template <int N, int QC, int QV>
+int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, double* gfc, double* gfv, double* gm,
+                double* tau, double nu_kk, cudaStream_t st) {
+  auto k = dg_geom_kernel<N, QC, QV>;
+  constexpr size_t smem = (table_elems<N, QC, QV>() + 3 * N * N * N + geom_buf_elems<N, QC, QV>() + 8) * sizeof(double);
+  if (smem > 227 * 1024) return -2;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    attr = true;
+  }
+  k<<<kp.Nc, NT, smem, st>>>(kp, xyz, gcc, gcv, gfc, gfv, gm, tau, nu_kk);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS>
+template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
 int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
               cudaStream_t st) {
-  auto k = dg_op_kernel<T, N, QC, QV, CB, CELL, FACE, MASS>;
+  auto k = dg_op_kernel<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>;
   constexpr size_t smem = op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS>();
   static bool attr = false;
   if (!attr) {
@@ -279,27 +535,36 @@ int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, v
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <typename T, int N, int QC, int QV>
-int op_dispatch(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
-                cudaStream_t st) {
+template <typename T, int N, int QC, int QV, int GEO>
+int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU,
+                    double* Uout, cudaStream_t st) {
   constexpr int CB = cells_per_cta<T, N, QC, QV>();
   switch (mode) {
-    case OP_CELL: return launch_op<T, N, QC, QV, CB, true, false, false>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_FACE: return launch_op<T, N, QC, QV, CB, false, true, false>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_MASS: return launch_op<T, N, QC, QV, CB, false, false, true>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_CELL | OP_FACE: return launch_op<T, N, QC, QV, CB, true, true, false>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_CELL: return launch_op<T, N, QC, QV, CB, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_FACE: return launch_op<T, N, QC, QV, CB, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_MASS: return launch_op<T, N, QC, QV, CB, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_CELL | OP_FACE:
+      return launch_op<T, N, QC, QV, CB, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_FACE | OP_MASS:
-      return launch_op<T, N, QC, QV, CB, true, true, true>(kp, U, Rin, Rout, dU, Uout, st);
+      return launch_op<T, N, QC, QV, CB, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
     default: return -2;
   }
 }
 
-template <typename TL, int N, int QC, int QV>
-int diag_launch(const KParams& kp, const double* U, const void* LU, double* partial, int* nblocks,
+template <typename T, int N, int QC, int QV>
+int op_dispatch(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
                 cudaStream_t st) {
+  if (kp.gcc == nullptr) return op_dispatch_geo<T, N, QC, QV, GEO_AFFINE>(mode, kp, U, Rin, Rout, dU, Uout, st);
+  return op_dispatch_geo<T, N, QC, QV, GEO_STORED>(mode, kp, U, Rin, Rout, dU, Uout, st);
+}
+
+template <typename TL, int N, int QC, int QV, int GEO>
+int diag_launch_geo(const KParams& kp, const double* U, const void* LU, double* partial, int* nblocks,
+                    cudaStream_t st) {
   constexpr int CB = QC * QC * QC > 300 ? 1 : 2;
-  auto k = dg_diag_kernel<TL, N, QC, QV, CB>;
-  constexpr size_t smem = diag_smem_bytes<N, QC, QV, CB>();
+  auto k = dg_diag_kernel<TL, N, QC, QV, CB, GEO>;
+  constexpr size_t smem = diag_smem_bytes<N, QC, QV, CB, GEO>();
+  if (smem > 227 * 1024) return -2;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
@@ -312,6 +577,13 @@ int diag_launch(const KParams& kp, const double* U, const void* LU, double* part
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <typename TL, int N, int QC, int QV>
+int diag_launch(const KParams& kp, const double* U, const void* LU, double* partial, int* nblocks,
+                cudaStream_t st) {
+  if (kp.gcc == nullptr) return diag_launch_geo<TL, N, QC, QV, GEO_AFFINE>(kp, U, LU, partial, nblocks, st);
+  return diag_launch_geo<TL, N, QC, QV, GEO_STORED>(kp, U, LU, partial, nblocks, st);
+}
+
 template <int N, int QC, int QV>
 Launchers make_launchers() {
   Launchers L;
@@ -319,6 +591,7 @@ Launchers make_launchers() {
   L.op_fp32 = op_dispatch<float, N, QC, QV>;
   L.diag_fp64 = diag_launch<double, N, QC, QV>;
   L.diag_fp32 = diag_launch<float, N, QC, QV>;
+  L.geom = geom_launch<N, QC, QV>;
   L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
   L.cb_fp32 = cells_per_cta<float, N, QC, QV>();
   return L;

@@ -14,9 +14,13 @@ using OpFn = int (*)(int mode, const KParams&, const double* U, const void* Rin,
 using DiagFn = int (*)(const KParams&, const double* U, const void* LU, double* partial, int* nblocks,
                        cudaStream_t);
 
+using GeomFn = int (*)(const KParams&, const double* xyz, double* gcc, double* gcv, double* gfc, double* gfv,
+                      double* gm, double* tau, double nu_kk, cudaStream_t);
+
 struct Launchers {
   OpFn op_fp64, op_fp32;
   DiagFn diag_fp64, diag_fp32;
+  GeomFn geom;
   int cb_fp64, cb_fp32;
 };
 

@@ -210,6 +210,8 @@ std::vector<double> build_tables(int k, int QC, int QV) {
   lagrange(xv, xv, Vg, Dg);
   put_eo(t, L.eo[EO_DV], Dg, QV, QV);
   put_eo(t, L.eo[EO_DVT], transpose(Dg, QV, QV), QV, QV);
+  lagrange(xm, xm, Vg, Dg);  // collocation derivative on the mass points (geometry)
+  put_eo(t, L.eo[EO_DM], Dg, N, N);
   lagrange(nodes, xm, V, D);  // square LGL-to-Gauss matrix at the k+1 mass points
   put_eo(t, L.eo[EO_SM], V, N, N);
   if (!invert(V, N)) return {};
@@ -253,6 +255,9 @@ struct dgcns_ctx {
   float* d_tab32 = nullptr;
   double* d_tau = nullptr;
   void* d_R = nullptr;        // residual scratch (split kernels)
+  double* g64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stored geometry, FP64 (gcc gcv gfc gfv gm)
+  float* g32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the mixed form
+  size_t gsize[5] = {0, 0, 0, 0, 0};
   double* d_partial = nullptr;
   int diag_blocks = 0;
   int64_t launches = 0;
@@ -293,6 +298,35 @@ static void map_point(const dgcns_mesh& m, double* x) {
   }
 }
 
+namespace {
+__global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// Node coordinates of the degree-k geometry on the host: [Nc][3][n^3].
+std::vector<double> host_node_coords(const dgcns_mesh& m, int k) {
+  const int N = k + 1, N3 = N * N * N;
+  std::vector<double> nodes = lgl(k);
+  symmetrize(nodes);
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (m.hi[d] - m.lo[d]) / m.n[d];
+  const long long Nc = (long long)m.n[0] * m.n[1] * m.n[2];
+  std::vector<double> host((size_t)Nc * 3 * N3);
+  for (long long e = 0; e < Nc; ++e) {
+    const int cc[3] = {(int)(e % m.n[0]), (int)((e / m.n[0]) % m.n[1]), (int)(e / ((long long)m.n[0] * m.n[1]))};
+    for (int i = 0; i < N3; ++i) {
+      const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = m.lo[d] + (cc[d] + nodes[ii[d]]) * h[d];
+      map_point(m, x);
+      for (int d = 0; d < 3; ++d) host[((size_t)e * 3 + d) * N3 + i] = x[d];
+    }
+  }
+  return host;
+}
+}  // namespace
+
 extern "C" {
 
 int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream, dgcns_ctx** out) {
@@ -325,8 +359,10 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     return bad(DGCNS_ERR_INVALID_ARG, "precision must be DGCNS_FP64 or DGCNS_MIXED");
   if (prm->kernel != DGCNS_KERNEL_SPLIT && prm->kernel != DGCNS_KERNEL_FUSED)
     return bad(DGCNS_ERR_INVALID_ARG, "kernel must be DGCNS_KERNEL_SPLIT or DGCNS_KERNEL_FUSED");
-  if (mesh->mapping != DGCNS_MAP_AFFINE)
-    return bad(DGCNS_ERR_UNSUPPORTED, "only affine (Cartesian) meshes are supported by this build");
+  if (mesh->mapping != DGCNS_MAP_AFFINE && mesh->mapping != DGCNS_MAP_CHANNEL && mesh->mapping != DGCNS_MAP_SINE)
+    return bad(DGCNS_ERR_INVALID_ARG, "unknown mapping");
+  if (mesh->mapping == DGCNS_MAP_CHANNEL && !(mesh->map_param > 0.0))
+    return bad(DGCNS_ERR_INVALID_ARG, "channel stretch factor must be positive");
   const long long ncell = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
   if (ncell > (1LL << 30)) return bad(DGCNS_ERR_INVALID_ARG, "too many cells");
   const int N = k + 1;
@@ -407,9 +443,77 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   kp.tau = c->d_tau;
   kp.conv = kp.visc = 1;
   kp.tables = prm->precision == DGCNS_MIXED ? (const void*)c->d_tab32 : (const void*)c->d_tab64;
+  if (mesh->mapping != DGCNS_MAP_AFFINE) {
+    // stored geometry: node coordinates -> Jacobians at every point set (FP64 kernel), tau per cell
+    const int QC = prm->nq_conv, QV = prm->nq_visc;
+    c->gsize[0] = (size_t)c->Nc * 10 * QC * QC * QC;
+    c->gsize[1] = (size_t)c->Nc * 10 * QV * QV * QV;
+    c->gsize[2] = (size_t)c->Nc * 6 * 13 * QC * QC;
+    c->gsize[3] = (size_t)c->Nc * 6 * 13 * QV * QV;
+    c->gsize[4] = (size_t)c->Nc * c->N3;
+    for (int i = 0; i < 5; ++i)
+      if (cudaMalloc(&c->g64[i], c->gsize[i] * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        dg_cns_destroy(c);
+        g_create_err = "out of device memory (geometry)";
+        return DGCNS_ERR_OOM;
+      }
+    std::vector<double> xyz = host_node_coords(*mesh, k);
+    double* d_xyz = nullptr;
+    if (cudaMalloc(&d_xyz, xyz.size() * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      dg_cns_destroy(c);
+      g_create_err = "out of device memory (coordinates)";
+      return DGCNS_ERR_OOM;
+    }
+    cudaMemcpy(d_xyz, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice);
+    KParams kg = kp;
+    kg.tables = c->d_tab64;
+    const int rg = c->L.geom(kg, d_xyz, c->g64[0], c->g64[1], c->g64[2], c->g64[3], c->g64[4], c->d_tau,
+                             c->nu * (k + 1) * (k + 1), c->stream);
+    c->launches += 1;
+    const cudaError_t se = cudaStreamSynchronize(c->stream);
+    cudaFree(d_xyz);
+    if (rg != 0 || se != cudaSuccess) {
+      g_create_err = rg == -2 ? "stored geometry not available for this (k, nq) (shared memory)" : "geometry kernel";
+      cudaGetLastError();
+      dg_cns_destroy(c);
+      return rg == -2 ? DGCNS_ERR_UNSUPPORTED : DGCNS_ERR_CUDA;
+    }
+    if (prm->precision == DGCNS_MIXED) {
+      for (int i = 0; i < 5; ++i) {
+        if (cudaMalloc(&c->g32[i], c->gsize[i] * sizeof(float)) != cudaSuccess) {
+          cudaGetLastError();
+          dg_cns_destroy(c);
+          g_create_err = "out of device memory (FP32 geometry)";
+          return DGCNS_ERR_OOM;
+        }
+        d2f_kernel<<<1024, 256, 0, c->stream>>>(c->g64[i], c->g32[i], c->gsize[i]);
+        c->launches += 1;
+      }
+      kp.gcc = c->g32[0];
+      kp.gcv = c->g32[1];
+      kp.gfc = c->g32[2];
+      kp.gfv = c->g32[3];
+      kp.gm = c->g32[4];
+    } else {
+      kp.gcc = c->g64[0];
+      kp.gcv = c->g64[1];
+      kp.gfc = c->g64[2];
+      kp.gfv = c->g64[3];
+      kp.gm = c->g64[4];
+    }
+  }
   // diagnostics partial sums
   KParams kd = kp;
   kd.tables = c->d_tab64;
+  if (c->g64[0]) {
+    kd.gcc = c->g64[0];
+    kd.gcv = c->g64[1];
+    kd.gfc = c->g64[2];
+    kd.gfv = c->g64[3];
+    kd.gm = c->g64[4];
+  }
   int nblk = 0;
   c->L.diag_fp64(kd, nullptr, nullptr, nullptr, &nblk, c->stream);
   c->diag_blocks = nblk;
@@ -434,6 +538,10 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_tau);
   cudaFree(c->d_R);
   cudaFree(c->d_partial);
+  for (int i = 0; i < 5; ++i) {
+    cudaFree(c->g64[i]);
+    cudaFree(c->g32[i]);
+  }
   delete c;
   return DGCNS_OK;
 }
@@ -455,23 +563,7 @@ int dg_cns_sizes(const dgcns_ctx* c, int64_t* nc, int64_t* nn, int64_t* nd) {
 int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (!xyz) return fail(c, DGCNS_ERR_INVALID_ARG, "xyz is NULL");
-  const dgcns_mesh& m = c->mesh;
-  const int N = c->N, N3 = c->N3;
-  std::vector<double> nodes = lgl(c->prm.k);
-  symmetrize(nodes);
-  double h[3];
-  for (int d = 0; d < 3; ++d) h[d] = (m.hi[d] - m.lo[d]) / m.n[d];
-  std::vector<double> host((size_t)c->Nc * 3 * N3);
-  for (int e = 0; e < c->Nc; ++e) {
-    const int cc[3] = {e % m.n[0], (e / m.n[0]) % m.n[1], e / (m.n[0] * m.n[1])};
-    for (int i = 0; i < N3; ++i) {
-      const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
-      double x[3];
-      for (int d = 0; d < 3; ++d) x[d] = m.lo[d] + (cc[d] + nodes[ii[d]]) * h[d];
-      map_point(m, x);
-      for (int d = 0; d < 3; ++d) host[((size_t)e * 3 + d) * N3 + i] = x[d];
-    }
-  }
+  const std::vector<double> host = host_node_coords(c->mesh, c->prm.k);
   if (cudaMemcpyAsync(xyz, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
@@ -569,11 +661,23 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
   return DGCNS_OK;
 }
 
+static KParams diag_params(const dgcns_ctx* c) {
+  KParams kp = c->kp;
+  kp.tables = c->d_tab64;
+  if (c->g64[0]) {
+    kp.gcc = c->g64[0];
+    kp.gcv = c->g64[1];
+    kp.gfc = c->g64[2];
+    kp.gfv = c->g64[3];
+    kp.gm = c->g64[4];
+  }
+  return kp;
+}
+
 int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* out) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (!U || !out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
-  KParams kp = c->kp;
-  kp.tables = c->d_tab64;
+  KParams kp = diag_params(c);
   int nblk = 0;
   const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
   if (f(kp, U, LU, c->d_partial, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics kernel launch");
@@ -651,8 +755,7 @@ extern "C" {
 int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, double* out_dev) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (!U || !out_dev) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
-  KParams kp = c->kp;
-  kp.tables = c->d_tab64;
+  KParams kp = diag_params(c);
   const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
   int nblk = 0;
   if (f(kp, nullptr, nullptr, nullptr, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics set-up");

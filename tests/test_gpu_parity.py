@@ -238,3 +238,75 @@ def test_unsupported_configuration():
     with pytest.raises(api.DGCNSError) as ei:
         DGCNS((2, 2, 2), (0, 0, 0), (1, 1, 1), (1, 1, 1), 3, 3, 3)
     assert ei.value.code == -1
+
+
+# -- non-affine meshes: stored geometry (channel stretching, sinusoidal deformation) ----------------------
+def pair_mapped(ncells, k, mapping, param, periodic, lo, hi, precision=0, kernel=1, Re=1600.0, u_mach=0.0,
+                body_force=(0.0, 0.0, 0.0)):
+    qc, qv = (3 * k) // 2 + 1, k + 1
+    g = DGCNS(ncells, lo, hi, periodic, k, qc, qv, Re=Re, u_mach=u_mach, body_force=body_force, precision=precision,
+              kernel=kernel, mapping=mapping, map_param=param)
+    mesh = BoxMesh(ncells, lo, hi, periodic, k, mapping, param)
+    phys = ph.Physics.from_numbers(Re, 0.71, 0.1, u_mach=(u_mach or None), body_force=body_force)
+    return g, DGOperator(mesh, phys, qc, qv)
+
+
+CHANNEL = dict(periodic=(1, 0, 1), lo=(0.0, -1.0, 0.0), hi=(2 * PI, 1.0, PI), Re=180.0, u_mach=18.3)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_channel_mesh_residual_and_L_fp64(kernel):
+    g, op = pair_mapped((2, 3, 2), 3, 1, 1.8, kernel=kernel, body_force=(1.0, 0.0, 0.0), **CHANNEL)
+    xyz = g.node_coords().cpu()
+    assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
+    U = inputs.channel_state(xyz, 1806)
+    ref, t2, tm = fp64_tol(op.residual, U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), ref)
+    assert l2 < t2 and mx < tm, (l2, mx, t2, tm)
+    ref, t2, tm = fp64_tol(op.L, U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), ref)
+    assert l2 < t2 and mx < tm, (l2, mx, t2, tm)
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_deformed_periodic_mesh_fp64(k, kernel):
+    g, op = pair_mapped((2, 2, 2), k, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 40 + k)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+def test_deformed_mesh_free_stream_on_gpu():
+    g, op = pair_mapped((3, 2, 2), 3, 2, 0.08, (1, 1, 1), (-PI,) * 3, (PI,) * 3)
+    U = torch.empty(g.shape, dtype=torch.float64)
+    for c, v in enumerate((1.1, 0.3, -0.2, 0.1, 180.0)):
+        U[:, c] = v
+    R = g.apply(on_gpu(U), op=api.OP_F).cpu()
+    assert float(R.abs().max()) < 1e-13 * 180.0 * 10
+
+
+def test_deformed_mesh_diagnostics_and_rk_step():
+    g, op = pair_mapped((2, 2, 2), 3, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3)
+    U = inputs.tgv_state(op.xyz)
+    LU = op.L(U)
+    ref = odiag.diagnostics(op, U, LU).numpy()
+    out = g.diagnostics(on_gpu(U), on_gpu(LU))
+    assert np.allclose(out[:8], ref[:8], rtol=1e-11, atol=1e-13), (out, ref)
+    dt = 1e-3
+    Ug = on_gpu(U)
+    g.rk_steps(2, dt, 0.0, Ug)
+    Ur = U
+    for i in range(2):
+        Ur = ork.step(lambda V, t: op.L(V), Ur, dt, i * dt)
+    l2, mx = rel_err(Ug - on_gpu(U), Ur - U)
+    assert l2 < 1e-9 and mx < 1e-9, (l2, mx)
+
+
+def test_channel_mixed_precision_error():
+    g, op = pair_mapped((2, 4, 2), 3, 1, 1.8, precision=1, body_force=(1.0, 0.0, 0.0), **CHANNEL)
+    U = inputs.channel_state(op.xyz, 1806)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < 1e-3 and mx < 1e-2, (l2, mx)
