@@ -282,7 +282,37 @@ def extras(args, cfg):
                                   "rel_max": float(d.abs().max() / L64.abs().max())}
     del g64, g32, U, L64, L32, d
     torch.cuda.empty_cache()
+    res["adjoint"] = adjoint_cost()
     return res
+
+
+def adjoint_cost(nsteps=200, every=20):
+    """Discrete adjoint of TGV 24^3, k = 4 (FP64): forward nsteps RK(5,4) steps with a checkpoint every `every`
+    steps, then the gradient of the final kinetic energy with respect to the initial velocity field (recomputation
+    of the segments + stage adjoints).  Reports forward and gradient times and their ratio."""
+    from paper_1806_03095_gb300 import adjoint as adj, configs, inputs
+    cfg = configs.WORKLOADS["tgv24_k4"](precision=0, kernel=1)
+    g = configs.make_context(cfg)
+    U0 = inputs.tgv_state(g.node_coords())
+    rho = U0[:, 0].clone()
+    u0 = (U0[:, 1:4] / rho[:, None]).clone().requires_grad_(True)
+    cv = cfg["R"] / (cfg["gamma"] - 1.0)
+    T0 = (1.0 / cfg["Ma"]) ** 2 / (cfg["gamma"] * cfg["R"])
+    dt = configs.time_step(cfg)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    Ui = torch.cat([rho[:, None], rho[:, None] * u0, (rho * (cv * T0 + 0.5 * (u0 * u0).sum(1)))[:, None]], 1)
+    J = adj.kinetic_energy(g, adj.integrate(g, Ui.contiguous(), nsteps, dt, every))
+    ev[1].record()
+    J.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    fwd = ev[0].elapsed_time(ev[1])
+    bwd = ev[1].elapsed_time(ev[2])
+    return {"workload": "TGV 24^3, k=4, FP64, %d RK(5,4) steps, checkpoint every %d" % (nsteps, every),
+            "forward_ms": round(fwd, 1), "gradient_ms": round(bwd, 1), "gradient_over_forward": round(bwd / fwd, 3),
+            "grad_norm": float(torch.linalg.norm(u0.grad)), "e_k_final": float(J)}
 
 
 # -- CPU oracle --------------------------------------------------------------------------------------

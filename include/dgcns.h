@@ -138,6 +138,27 @@ int dg_cns_rk_stage(dgcns_ctx* ctx, int stage, double dt, double t, const double
  * caller-provided work arrays. */
 int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU);
 
+/* Adjoint (vector-Jacobian product) of the operator of dg_cns_apply(DGCNS_OP_L):
+ *   G = (dL/dU)^T W = -(dF/dU)^T M^-1 W     (M symmetric)
+ * evaluated by transposed sum factorization and transposed pointwise flux
+ * Jacobians (LLF, F_c, F_v, the SIPG terms and the wall state), faces
+ * element-centric.  Not in the paper (it is forward-only): the transpose of
+ * Eq. WeakFormulationConservedVariables as discretised here.  U: double state;
+ * W, G: residual type; G must not alias U.  UNSUPPORTED with a body force. */
+int dg_cns_adjoint_apply(dgcns_ctx* ctx, const double* U, const void* W, void* G);
+
+/* Adjoint of one stage of dg_cns_rk_stage (reverse of dU <- A dU + dt L(U_in),
+ * U_out <- U_in + B dU).  On entry lam_U (double) and lam_dU (residual type)
+ * are the adjoints of (U_out, dU after the stage); on return those of (U_in,
+ * dU before the stage):  W = lam_dU + B lam_U;  lam_U += dt (dL/dU)^T W;
+ * lam_dU = A W.  U_in is the stage's input state (recomputed from a
+ * checkpoint by the caller).  Uses the context's residual scratch. */
+int dg_cns_rk_stage_adjoint(dgcns_ctx* ctx, int stage, double dt, const double* U_in, double* lam_U, void* lam_dU);
+
+/* G = d e_k / dU (double, state layout) for e_k of dg_cns_diagnostics: the
+ * seed of the discrete adjoint of the final kinetic energy. */
+int dg_cns_kinetic_energy_gradient(dgcns_ctx* ctx, const double* U, double* G);
+
 /* Taylor--Green diagnostics of Sec. 4.2.3 in FP64 (Gauss rule nq_conv):
  * out[0] e_k = 1/V int |u|^2/2, out[1] eps = nu/V int grad u : grad u,
  * out[2] -de_k/dt from L_of_U (0 when L_of_U is NULL), out[3..7] int rho,

@@ -149,6 +149,30 @@ class DGCNS:
         self._check(self.lib.dg_cns_diagnostics_noalloc(self.ctx, _ptr(U), _ptr(LU), _ptr(out)))
         return out
 
+    def dg_cns_adjoint_apply(self, U, W, G=None):
+        """G = (dL/dU)^T W (residual type)."""
+        self._state(U, "U")
+        self._state(W, "W", self.rdtype)
+        G = self.empty_residual() if G is None else self._state(G, "G", self.rdtype)
+        self._sync_stream()
+        self._check(self.lib.dg_cns_adjoint_apply(self.ctx, _ptr(U), _ptr(W), _ptr(G)))
+        return G
+
+    def dg_cns_rk_stage_adjoint(self, stage, dt, U_in, lam_U, lam_dU):
+        self._state(U_in, "U_in")
+        self._state(lam_U, "lam_U")
+        self._state(lam_dU, "lam_dU", self.rdtype)
+        self._sync_stream()
+        self._check(self.lib.dg_cns_rk_stage_adjoint(self.ctx, int(stage), float(dt), _ptr(U_in), _ptr(lam_U),
+                                                     _ptr(lam_dU)))
+
+    def dg_cns_kinetic_energy_gradient(self, U, G=None):
+        self._state(U, "U")
+        G = self.empty_state() if G is None else self._state(G, "G")
+        self._sync_stream()
+        self._check(self.lib.dg_cns_kinetic_energy_gradient(self.ctx, _ptr(U), _ptr(G)))
+        return G
+
     def dg_cns_launch_count(self):
         c = ctypes.c_int64()
         self._check(self.lib.dg_cns_launch_count(self.ctx, ctypes.byref(c)))
@@ -171,6 +195,9 @@ class DGCNS:
     rk_stage = dg_cns_rk_stage
     rk_steps = dg_cns_rk_steps
     diagnostics = dg_cns_diagnostics
+    adjoint_apply = dg_cns_adjoint_apply
+    rk_stage_adjoint = dg_cns_rk_stage_adjoint
+    kinetic_energy_gradient = dg_cns_kinetic_energy_gradient
     node_coords = dg_cns_node_coords
 
 

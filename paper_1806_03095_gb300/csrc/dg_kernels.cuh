@@ -22,6 +22,8 @@
 
 namespace dgcns {
 
+constexpr int NT = 128;  // threads per CTA of every operator kernel
+
 // ---------------------------------------------------------------------------
 // Shared-memory tables
 // ---------------------------------------------------------------------------

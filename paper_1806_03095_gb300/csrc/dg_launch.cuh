@@ -3,12 +3,12 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dg_adjoint.cuh"
 #include "dg_kernels.cuh"
 #include "dg_launchers.h"
 
 namespace dgcns {
 
-constexpr int NT = 128;  // threads per CTA
 
 // Cells per CTA: the largest batch (<= 8) whose shared memory stays below ~112 KB,
 // so that two CTAs fit on one SM (228 KB).
@@ -437,7 +437,7 @@ constexpr int geom_buf_elems() {
 template <int N, int QC, int QV>
 __global__ void __launch_bounds__(NT) dg_geom_kernel(const KParams kp, const double* __restrict__ xyz,
                                                      double* gcc, double* gcv, double* gfc, double* gfv, double* gm,
-                                                     double* tau, double nu_kk) {
+                                                     double* tau, double* vol, double nu_kk) {
   constexpr int N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sm = reinterpret_cast<double*>(smem_raw);
@@ -499,12 +499,15 @@ __global__ void __launch_bounds__(NT) dg_geom_kernel(const KParams kp, const dou
       }
       __syncthreads();
     }
-  if (threadIdx.x == 0) tau[e] = nu_kk * (0.5 * red[1] + red[2]) / red[0];
+  if (threadIdx.x == 0) {
+    tau[e] = nu_kk * (0.5 * red[1] + red[2]) / red[0];
+    vol[e] = red[0];
+  }
 }
 
 template <int N, int QC, int QV>
 int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, double* gfc, double* gfv, double* gm,
-                double* tau, double nu_kk, cudaStream_t st) {
+                double* tau, double* vol, double nu_kk, cudaStream_t st) {
   auto k = dg_geom_kernel<N, QC, QV>;
   constexpr size_t smem = (table_elems<N, QC, QV>() + 3 * N * N * N + geom_buf_elems<N, QC, QV>() + 8) * sizeof(double);
   if (smem > 227 * 1024) return -2;
@@ -513,8 +516,86 @@ int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, 
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
     attr = true;
   }
-  k<<<kp.Nc, NT, smem, st>>>(kp, xyz, gcc, gcv, gfc, gfv, gm, tau, nu_kk);
+  k<<<kp.Nc, NT, smem, st>>>(kp, xyz, gcc, gcv, gfc, gfv, gm, tau, vol, nu_kk);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of the kinetic energy e_k = (1/V) int |u|^2/2, u = m/rho (convective Gauss
+// rule, as dg_diag_kernel) with respect to the nodal state (FP64):
+//   d/d rho_j = (1/V) sum_q (-|u|^2/rho) |J| w phi_j(x_q),  d/d m_j = (1/V) sum_q (u/rho) |J| w phi_j(x_q).
+// ---------------------------------------------------------------------------
+template <int N, int QC, int QV, int CB, int GEO>
+__global__ void __launch_bounds__(NT) dg_ekgrad_kernel(const KParams kp, const double* __restrict__ U,
+                                                       double* __restrict__ G, double inv_volume) {
+  constexpr int N3 = N * N * N, P = QC * QC * QC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* stab = sm;
+  double* su = stab + table_elems<N, QC, QV>();
+  double* V0 = su + CB * 5 * N3;
+  double* V1 = V0 + CB * 5 * P;
+  double* V2 = V1 + CB * 5 * P;
+  const Tab<double> tb = load_tables<double, N, QC, QV>(static_cast<const double*>(kp.tables), stab);
+  const int e0 = blockIdx.x * CB;
+  const int nb = min(CB, kp.Nc - e0);
+  if (nb <= 0) return;
+  const size_t base = (size_t)e0 * 5 * N3;
+  const int nvals = nb * 5 * N3, nbl = nb * 5;
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) su[i] = U[base + i];
+  __syncthreads();
+  sweep<double, 0, N, N, N, QC, 1, false>(su, V1, tb.eSc, nbl);
+  __syncthreads();
+  sweep<double, 1, QC, N, N, QC, 1, false>(V1, V2, tb.eSc, nbl);
+  __syncthreads();
+  sweep<double, 2, QC, QC, N, QC, 1, false>(V2, V0, tb.eSc, nbl);
+  __syncthreads();
+  const double detJ = kp.h[0] * kp.h[1] * kp.h[2];
+  const double* gcc = static_cast<const double*>(kp.gcc);
+  for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+    const int e = idx / P, p = idx - e * P;
+    const int o = e * 5 * P + p;
+    const double w = tb.wc[p % QC] * tb.wc[(p / QC) % QC] * tb.wc[p / (QC * QC)] *
+                     (GEO == GEO_AFFINE ? detJ : gcc[((size_t)(e0 + e) * 10 + 9) * P + p]) * inv_volume;
+    // e = |u|^2 / 2 with u = m / rho:  de/drho = -|u|^2 / rho,  de/dm = u / rho
+    const double rinv = 1.0 / V0[o];
+    const double u0 = V0[o + P] * rinv, u1 = V0[o + 2 * P] * rinv, u2 = V0[o + 3 * P] * rinv;
+    const double wr = w * rinv;
+    V0[o] = -(u0 * u0 + u1 * u1 + u2 * u2) * wr;
+    V0[o + P] = u0 * wr;
+    V0[o + 2 * P] = u1 * wr;
+    V0[o + 3 * P] = u2 * wr;
+    V0[o + 4 * P] = 0.0;
+  }
+  __syncthreads();
+  sweep<double, 2, QC, QC, QC, N, 1, false>(V0, V1, tb.eScT, nbl);
+  __syncthreads();
+  sweep<double, 1, QC, QC, N, N, 1, false>(V1, V2, tb.eScT, nbl);
+  __syncthreads();
+  sweep<double, 0, QC, N, N, N, 1, false>(V2, su, tb.eScT, nbl);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) G[base + i] = su[i];
+}
+
+template <int N, int QC, int QV, int GEO>
+int ekgrad_launch_geo(const KParams& kp, const double* U, double* G, double inv_volume, cudaStream_t st) {
+  constexpr int CB = QC * QC * QC > 300 ? 1 : 2;
+  constexpr size_t smem = (table_elems<N, QC, QV>() + CB * 5 * N * N * N + 3 * CB * 5 * QC * QC * QC) * sizeof(double) + 64;
+  if (smem > 227 * 1024) return -2;
+  auto k = dg_ekgrad_kernel<N, QC, QV, CB, GEO>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    attr = true;
+  }
+  k<<<(kp.Nc + CB - 1) / CB, NT, smem, st>>>(kp, U, G, inv_volume);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int N, int QC, int QV>
+int ekgrad_launch(const KParams& kp, const double* U, double* G, double inv_volume, cudaStream_t st) {
+  if (kp.gcc == nullptr) return ekgrad_launch_geo<N, QC, QV, GEO_AFFINE>(kp, U, G, inv_volume, st);
+  return ekgrad_launch_geo<N, QC, QV, GEO_STORED>(kp, U, G, inv_volume, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,6 +673,11 @@ Launchers make_launchers() {
   L.diag_fp64 = diag_launch<double, N, QC, QV>;
   L.diag_fp32 = diag_launch<float, N, QC, QV>;
   L.geom = geom_launch<N, QC, QV>;
+  L.adj_fp64 = adj_launch<double, N, QC, QV>;
+  L.adj_fp32 = adj_launch<float, N, QC, QV>;
+  L.prep_fp64 = adj_prep_launch<double>;
+  L.prep_fp32 = adj_prep_launch<float>;
+  L.ekgrad = ekgrad_launch<N, QC, QV>;
   L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
   L.cb_fp32 = cells_per_cta<float, N, QC, QV>();
   return L;

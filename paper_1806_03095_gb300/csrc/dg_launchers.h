@@ -15,12 +15,21 @@ using DiagFn = int (*)(const KParams&, const double* U, const void* LU, double* 
                        cudaStream_t);
 
 using GeomFn = int (*)(const KParams&, const double* xyz, double* gcc, double* gcv, double* gfc, double* gfv,
-                      double* gm, double* tau, double nu_kk, cudaStream_t);
+                      double* gm, double* tau, double* vol, double nu_kk, cudaStream_t);
+
+// Adjoint: G = -(dF/dU)^T Y (lamU == nullptr) or lamU += dt * that (out_mode 2 in kp).
+using AdjFn = int (*)(const KParams&, const double* U, const void* Y, void* G, double* lamU, cudaStream_t);
+using PrepFn = int (*)(size_t n, double A, double B, const double* lamU, void* lamdU, void* W, cudaStream_t);
+// G = d e_k / dU (FP64), e_k = (1/V) int |u|^2 / 2 at the convective points.
+using EkGradFn = int (*)(const KParams&, const double* U, double* G, double inv_volume, cudaStream_t);
 
 struct Launchers {
   OpFn op_fp64, op_fp32;
   DiagFn diag_fp64, diag_fp32;
   GeomFn geom;
+  AdjFn adj_fp64, adj_fp32;
+  PrepFn prep_fp64, prep_fp32;
+  EkGradFn ekgrad;
   int cb_fp64, cb_fp32;
 };
 

@@ -261,6 +261,7 @@ struct dgcns_ctx {
   double* d_partial = nullptr;
   int diag_blocks = 0;
   int64_t launches = 0;
+  double volume = 0.0;  // domain volume (Gauss sum at the convective points)
   std::string err;
 };
 
@@ -442,6 +443,7 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   kp.rhoE_ref = prm->rho0 * c->cv * c->Tw;
   kp.tau = c->d_tau;
   kp.conv = kp.visc = 1;
+  c->volume = (mesh->hi[0] - mesh->lo[0]) * (mesh->hi[1] - mesh->lo[1]) * (mesh->hi[2] - mesh->lo[2]);
   kp.tables = prm->precision == DGCNS_MIXED ? (const void*)c->d_tab32 : (const void*)c->d_tab64;
   if (mesh->mapping != DGCNS_MAP_AFFINE) {
     // stored geometry: node coordinates -> Jacobians at every point set (FP64 kernel), tau per cell
@@ -469,11 +471,27 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     cudaMemcpy(d_xyz, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice);
     KParams kg = kp;
     kg.tables = c->d_tab64;
-    const int rg = c->L.geom(kg, d_xyz, c->g64[0], c->g64[1], c->g64[2], c->g64[3], c->g64[4], c->d_tau,
+    double* d_vol = nullptr;
+    if (cudaMalloc(&d_vol, (size_t)c->Nc * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_xyz);
+      dg_cns_destroy(c);
+      g_create_err = "out of device memory (volumes)";
+      return DGCNS_ERR_OOM;
+    }
+    const int rg = c->L.geom(kg, d_xyz, c->g64[0], c->g64[1], c->g64[2], c->g64[3], c->g64[4], c->d_tau, d_vol,
                              c->nu * (k + 1) * (k + 1), c->stream);
     c->launches += 1;
     const cudaError_t se = cudaStreamSynchronize(c->stream);
     cudaFree(d_xyz);
+    if (rg == 0 && se == cudaSuccess) {
+      std::vector<double> vol(c->Nc);
+      cudaMemcpy(vol.data(), d_vol, vol.size() * sizeof(double), cudaMemcpyDeviceToHost);
+      double v = 0.0;
+      for (double x : vol) v += x;
+      c->volume = v;
+    }
+    cudaFree(d_vol);
     if (rg != 0 || se != cudaSuccess) {
       g_create_err = rg == -2 ? "stored geometry not available for this (k, nq) (shared memory)" : "geometry kernel";
       cudaGetLastError();
@@ -658,6 +676,70 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
     if (cudaMemcpyAsync(U, a, c->state_elems * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
       return cuda_fail(c, "state copy");
   }
+  return DGCNS_OK;
+}
+
+int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U || !W || !G) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
+  if (G == (const void*)U) return fail(c, DGCNS_ERR_INVALID_ARG, "G must not alias U");
+  KParams km = c->kp;
+  km.out_mode = 0;
+  km.has_bf = 0;
+  int r = run_op(c, OP_MASS, km, nullptr, W, c->d_R, nullptr, nullptr);  // Y = M^-1 W
+  if (r) return r;
+  KParams ka = c->kp;
+  ka.out_mode = 0;
+  const AdjFn f = c->prm.precision == DGCNS_MIXED ? c->L.adj_fp32 : c->L.adj_fp64;
+  const int ra = f(ka, U, c->d_R, G, nullptr, c->stream);
+  c->launches += 1;
+  if (ra == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint kernel does not fit shared memory for this (k, nq)");
+  if (ra) return cuda_fail(c, "adjoint kernel launch");
+  return DGCNS_OK;
+}
+
+int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_in, double* lam_U, void* lam_dU) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
+  if (!U_in || !lam_U || !lam_dU) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
+  if ((const void*)lam_U == (const void*)U_in) return fail(c, DGCNS_ERR_INVALID_ARG, "lam_U must not alias U_in");
+  const PrepFn prep = c->prm.precision == DGCNS_MIXED ? c->L.prep_fp32 : c->L.prep_fp64;
+  // W = lam_dU + B lam_U (scratch), lam_dU <- A W
+  if (prep(c->state_elems, RK_A[stage], RK_B[stage], lam_U, lam_dU, c->d_R, c->stream) != 0)
+    return cuda_fail(c, "adjoint stage preparation");
+  c->launches += 1;
+  KParams km = c->kp;
+  km.out_mode = 0;
+  km.has_bf = 0;
+  int r = run_op(c, OP_MASS, km, nullptr, c->d_R, c->d_R, nullptr, nullptr);  // Y = M^-1 W in place
+  if (r) return r;
+  KParams ka = c->kp;
+  ka.out_mode = 2;
+  ka.dt = dt;
+  const AdjFn f = c->prm.precision == DGCNS_MIXED ? c->L.adj_fp32 : c->L.adj_fp64;
+  const int ra = f(ka, U_in, c->d_R, nullptr, lam_U, c->stream);
+  c->launches += 1;
+  if (ra == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint kernel does not fit shared memory for this (k, nq)");
+  if (ra) return cuda_fail(c, "adjoint kernel launch");
+  return DGCNS_OK;
+}
+
+int dg_cns_kinetic_energy_gradient(dgcns_ctx* c, const double* U, double* G) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U || !G || (const void*)U == (const void*)G) return fail(c, DGCNS_ERR_INVALID_ARG, "bad arrays");
+  KParams kp = c->kp;
+  kp.tables = c->d_tab64;
+  if (c->g64[0]) {
+    kp.gcc = c->g64[0];
+    kp.gm = c->g64[4];
+  }
+  const int r = c->L.ekgrad(kp, U, G, 1.0 / c->volume, c->stream);
+  c->launches += 1;
+  if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "kinetic-energy gradient does not fit shared memory");
+  if (r) return cuda_fail(c, "kinetic-energy gradient launch");
   return DGCNS_OK;
 }
 

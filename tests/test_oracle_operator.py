@@ -362,3 +362,15 @@ def test_what_splits_add_up():
     op = make_op(mesh)
     U = inputs.random_state(mesh.Nc, mesh.n ** 3, 6)
     assert torch.allclose(op.residual(U, WHAT_CONV) + op.residual(U, WHAT_VISC), op.residual(U), rtol=1e-12, atol=1e-11)
+
+
+def test_oracle_tangent_linear_model_matches_finite_differences():
+    """The oracle's forward-mode derivative of L (used as the adjoint's reference) against central differences."""
+    mesh = tgv_mesh(2, 2)
+    op = make_op(mesh)
+    U = inputs.random_state(mesh.Nc, mesh.n ** 3, 90)
+    V = inputs.uniform(U.shape, 91)
+    JV = jvp(op.L, (U,), (V,))[1]
+    h = 1e-6
+    fd = (op.L(U + h * V) - op.L(U - h * V)) / (2 * h)
+    assert float(torch.linalg.norm(JV - fd) / torch.linalg.norm(JV)) < 1e-7
