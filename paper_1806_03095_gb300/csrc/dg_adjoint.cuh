@@ -47,10 +47,11 @@ __device__ __forceinline__ void cell_geo(const KParams& kp, const void* g, int P
   if (GEO == GEO_AFFINE) {
 #pragma unroll
     for (int m = 0; m < 9; ++m) Ji[m] = T(0);
-    Ji[0] = T(1.0 / kp.h[0]);
-    Ji[4] = T(1.0 / kp.h[1]);
-    Ji[8] = T(1.0 / kp.h[2]);
-    jw = wq * T(kp.h[0] * kp.h[1] * kp.h[2]);
+    const KConst<T>& kc = kconst<T>(kp);
+    Ji[0] = kc.hinv[0];
+    Ji[4] = kc.hinv[1];
+    Ji[8] = kc.hinv[2];
+    jw = wq * kc.detJ;
   } else {
     const T* gg = static_cast<const T*>(g) + cell * 10 * P + p;
 #pragma unroll
@@ -197,15 +198,15 @@ __device__ __forceinline__ void face_geo(const KParams& kp, const void* g, int P
   if (GEO == GEO_AFFINE) {
 #pragma unroll
     for (int m = 0; m < 9; ++m) Jm[m] = T(0);
-    Jm[0] = T(1.0 / kp.h[0]);
-    Jm[4] = T(1.0 / kp.h[1]);
-    Jm[8] = T(1.0 / kp.h[2]);
+    const KConst<T>& kc = kconst<T>(kp);
+    Jm[0] = kc.hinv[0];
+    Jm[4] = kc.hinv[1];
+    Jm[8] = kc.hinv[2];
 #pragma unroll
     for (int m = 0; m < 9; ++m) Jp[m] = Jm[m];
     n[0] = n[1] = n[2] = T(0);
     n[d] = s ? T(1) : T(-1);
-    constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    w = wq * T(kp.h[t1] * kp.h[t2]);
+    w = wq * kc.area[d];
   } else {
     const T* gg = static_cast<const T*>(g) + (cell * 6 + f) * 13 * P + p;
 #pragma unroll
@@ -506,16 +507,7 @@ __global__ void __launch_bounds__(NT) dg_adj_kernel(const KParams kp, const doub
   const int nb = min(CB, kp.Nc - e0);
   if (nb <= 0) return;
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
-  PhysT<T> ph;
-  ph.gamma = T(kp.gamma);
-  ph.gm1 = T(kp.gamma - 1.0);
-  ph.mu = T(kp.mu);
-  ph.lam_cv = T(kp.lam / kp.cv);
-  ph.rho_r = T(kp.rho_ref);
-  ph.rhoE_r = T(kp.rhoE_ref);
-  ph.p_r = T((kp.gamma - 1.0) * kp.rhoE_ref);
-  ph.H_r = T(kp.gamma * kp.rhoE_ref);
-  ph.cvTw2 = T(2.0 * kp.cv * kp.Tw);
+  const PhysT<T> ph = make_phys<T>(kp);
   const size_t base = (size_t)e0 * 5 * N3;
   const int nvals = nb * 5 * N3;
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {

@@ -46,6 +46,17 @@ constexpr TableLayout make_layout(int N, int QC, int QV) {
   return L;
 }
 
+// Constants precomputed on the host in the kernel's precision, so that the FP32
+// kernels issue no FP64 instruction for them (GB300 has 2 FP64 units per SM).
+template <typename T>
+struct KConst {
+  T hinv[3], detJ, area[3];  // affine geometry: 1/h_d, h0 h1 h2, face area h_t1 h_t2 per direction d
+  T gamma, gm1, mu, lam_cv;  // gamma, gamma - 1, mu, lambda / c_v
+  T rho_r, rhoE_r, p_r, H_r; // reference state, its pressure and rhoE_r + p_r
+  T cvTw2;                   // 2 c_v T_wall
+  T bf[3];                   // body force
+};
+
 // Per-launch parameters (passed by value).
 struct KParams {
   int Nc;
@@ -69,7 +80,31 @@ struct KParams {
   //   area element dA = |det J| |J^{-T} n_xi| (1), face f = 2d + s;  gm [Nc][N^3]: |det J| at
   //   the k+1 mass points.
   const void *gcc, *gcv, *gfc, *gfv, *gm;
+  // Optional deviation state U - U_ref already converted to the kernel's precision (same layout as U);
+  // when set, the operator kernels read own and neighbour values from it instead of converting U.
+  const void* Udev;
+  KConst<double> cd;
+  KConst<float> cf;
 };
+
+template <typename T>
+void fill_kconst(const KParams& kp, KConst<T>& c) {
+  for (int d = 0; d < 3; ++d) {
+    c.hinv[d] = T(1.0 / kp.h[d]);
+    c.area[d] = T(kp.h[(d + 1) % 3] * kp.h[(d + 2) % 3]);
+    c.bf[d] = T(kp.bf[d]);
+  }
+  c.detJ = T(kp.h[0] * kp.h[1] * kp.h[2]);
+  c.gamma = T(kp.gamma);
+  c.gm1 = T(kp.gamma - 1.0);
+  c.mu = T(kp.mu);
+  c.lam_cv = T(kp.lam / kp.cv);
+  c.rho_r = T(kp.rho_ref);
+  c.rhoE_r = T(kp.rhoE_ref);
+  c.p_r = T((kp.gamma - 1.0) * kp.rhoE_ref);
+  c.H_r = T(kp.gamma * kp.rhoE_ref);
+  c.cvTw2 = T(2.0 * kp.cv * kp.Tw);
+}
 
 constexpr int GEO_AFFINE = 0, GEO_STORED = 1;
 

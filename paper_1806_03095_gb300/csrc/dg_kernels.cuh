@@ -18,11 +18,27 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "dg_common.h"
 
 namespace dgcns {
 
 constexpr int NT = 128;  // threads per CTA of every operator kernel
+
+// Thread groups that cooperate on a batch of cells: the whole CTA (barrier
+// __syncthreads) or one warp (barrier __syncwarp, so warps of one CTA progress
+// independently and hide each other's latency).
+struct CtaGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int size() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
 
 // ---------------------------------------------------------------------------
 // Shared-memory tables
@@ -50,6 +66,40 @@ constexpr int table_elems() {
   return make_layout(N, QC, QV).total;
 }
 
+// 16-byte vector loads/stores of K contiguous values (K * sizeof(T) a multiple of 16, p 16-byte aligned).
+template <typename T, int K>
+__device__ __forceinline__ void vec_load(const T* p, T* x) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j) {
+      const float4 t = reinterpret_cast<const float4*>(p)[j];
+      x[4 * j] = t.x;
+      x[4 * j + 1] = t.y;
+      x[4 * j + 2] = t.z;
+      x[4 * j + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < K / 2; ++j) {
+      const double2 t = reinterpret_cast<const double2*>(p)[j];
+      x[2 * j] = t.x;
+      x[2 * j + 1] = t.y;
+    }
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void vec_store(T* p, const T* x) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j)
+      reinterpret_cast<float4*>(p)[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < K / 2; ++j) reinterpret_cast<double2*>(p)[j] = make_double2(x[2 * j], x[2 * j + 1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 1D sweep with even-odd decomposition: apply the operator O (DOUT x DIN, in
 // the even-odd form above, symmetry SYM = +1 or -1) along axis AX of nblk
@@ -57,9 +107,9 @@ constexpr int table_elems() {
 // other).  The axis extent DIN becomes DOUT.  One thread per line, the line in
 // registers, the operator broadcast from shared memory.  ACC adds into out.
 // ---------------------------------------------------------------------------
-template <typename T, int AX, int D0, int D1, int D2, int DOUT, int SYM, bool ACC>
+template <typename T, int AX, int D0, int D1, int D2, int DOUT, int SYM, bool ACC, class G = CtaGroup>
 __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ E,
-                                      int nblk) {
+                                      int nblk, G grp = G()) {
   constexpr int DIN = AX == 0 ? D0 : (AX == 1 ? D1 : D2);
   constexpr int IH = DIN / 2, OH = (DOUT + 1) / 2;
   constexpr int O0 = AX == 0 ? DOUT : D0;
@@ -72,7 +122,7 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
   const T* __restrict__ A = E;
   const T* __restrict__ B = E + OH * IH;
   const T* __restrict__ C = E + 2 * OH * IH;
-  for (int l = threadIdx.x; l < nblk * NL; l += blockDim.x) {
+  for (int l = grp.rank(); l < nblk * NL; l += grp.size()) {
     const int blk = l / NL, r = l - blk * NL;
     int ib, ob;
     if (AX == 0) {
@@ -88,15 +138,25 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
     }
     const T* ip = in + blk * ISZ + ib;
     T* op = out + blk * OSZ + ob;
+    // a line along x is contiguous: 16-byte vector accesses avoid the bank conflicts
+    // of threads reading 4-word lines at a 4-word stride
+    constexpr bool VIN = AX == 0 && (DIN * sizeof(T)) % 16 == 0;
+    constexpr bool VOUT = AX == 0 && (DOUT * sizeof(T)) % 16 == 0;
+    T x[DIN];
+    if (VIN && (reinterpret_cast<uintptr_t>(ip) & 15) == 0) {
+      vec_load<T, DIN>(ip, x);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIN; ++i) x[i] = ip[i * IST];
+    }
     T xe[IH], xo[IH];
-    T xm = T(0);
 #pragma unroll
     for (int i = 0; i < IH; ++i) {
-      const T lo = ip[i * IST], hi = ip[(DIN - 1 - i) * IST];
-      xe[i] = lo + hi;
-      xo[i] = lo - hi;
+      xe[i] = x[i] + x[DIN - 1 - i];
+      xo[i] = x[i] - x[DIN - 1 - i];
     }
-    if (DIN & 1) xm = ip[IH * IST];
+    const T xm = (DIN & 1) ? x[IH] : T(0);
+    T y[DOUT];
 #pragma unroll
     for (int q = 0; q < OH; ++q) {
       T e = (DIN & 1) ? C[q] * xm : T(0);
@@ -107,16 +167,27 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
         o += B[q * IH + i] * xo[i];
       }
       if ((DOUT & 1) && q == OH - 1) {
-        if (ACC) op[q * OST] += e + o; else op[q * OST] = e + o;
+        y[q] = e + o;
       } else {
-        const T lo = e + o, hi = SYM > 0 ? e - o : o - e;
-        if (ACC) {
-          op[q * OST] += lo;
-          op[(DOUT - 1 - q) * OST] += hi;
-        } else {
-          op[q * OST] = lo;
-          op[(DOUT - 1 - q) * OST] = hi;
-        }
+        y[q] = e + o;
+        y[DOUT - 1 - q] = SYM > 0 ? e - o : o - e;
+      }
+    }
+    if (VOUT && (reinterpret_cast<uintptr_t>(op) & 15) == 0) {
+      if (ACC) {
+        T z[DOUT];
+        vec_load<T, DOUT>(op, z);
+#pragma unroll
+        for (int q = 0; q < DOUT; ++q) y[q] += z[q];
+      }
+      vec_store<T, DOUT>(op, y);
+    } else {
+#pragma unroll
+      for (int q = 0; q < DOUT; ++q) {
+        if (ACC)
+          op[q * OST] += y[q];
+        else
+          op[q * OST] = y[q];
       }
     }
   }
@@ -191,6 +262,29 @@ __device__ __forceinline__ void visc_flux(const T u[5], const T G[5][3], const P
   }
 }
 
+template <typename T>
+__device__ __forceinline__ const KConst<T>& kconst(const KParams& kp);
+template <>
+__device__ __forceinline__ const KConst<double>& kconst<double>(const KParams& kp) { return kp.cd; }
+template <>
+__device__ __forceinline__ const KConst<float>& kconst<float>(const KParams& kp) { return kp.cf; }
+
+template <typename T>
+__device__ __forceinline__ PhysT<T> make_phys(const KParams& kp) {
+  const KConst<T>& c = kconst<T>(kp);
+  PhysT<T> ph;
+  ph.gamma = c.gamma;
+  ph.gm1 = c.gm1;
+  ph.mu = c.mu;
+  ph.lam_cv = c.lam_cv;
+  ph.rho_r = c.rho_r;
+  ph.rhoE_r = c.rhoE_r;
+  ph.p_r = c.p_r;
+  ph.H_r = c.H_r;
+  ph.cvTw2 = c.cvTw2;
+  return ph;
+}
+
 // Exterior state on an isothermal no-slip wall: rho+ = rho-, u+ = -u-, T+ = 2 T_w - T-,
 // i.e. rho E+ = 2 rho c_v T_w - rho E- + rho |u|^2, written for deviations
 // (rho E_r = rho_r c_v T_w):  d(rho E)+ = 2 c_v T_w d(rho) - d(rho E)- + |m|^2/rho.
@@ -237,12 +331,12 @@ struct Sizes {
 // su, sr: [CB][5][N^3]; ar: arena of CB*CELL_ARENA elements.
 // Affine geometry: J = diag(h), |J| = h0 h1 h2.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, int GEO>
+template <typename T, int N, int QC, int QV, int CB, int GEO, class G = CtaGroup>
 __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph,
-                           int e0, int nb) {
-  const T h[3] = {T(kp.h[0]), T(kp.h[1]), T(kp.h[2])};
-  const T detJ = h[0] * h[1] * h[2];
-  const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
+                           int e0, int nb, G grp = G()) {
+  const KConst<T>& kc = kconst<T>(kp);
+  const T detJ = kc.detJ;
+  const T hinv[3] = {kc.hinv[0], kc.hinv[1], kc.hinv[2]};
   const int nbl = nb * 5;
   if (kp.conv) {
     constexpr int P = QC * QC * QC;
@@ -251,14 +345,14 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
     T* F2 = ar + 2 * CB * 5 * P;
     T* G = ar + 3 * CB * 5 * P;
     // interpolate to the convective Gauss grid (Eq. SumFactorization)
-    sweep<T, 0, N, N, N, QC, 1, false>(su, F1, tb.eSc, nbl);
-    __syncthreads();
-    sweep<T, 1, QC, N, N, QC, 1, false>(F1, F2, tb.eSc, nbl);
-    __syncthreads();
-    sweep<T, 2, QC, QC, N, QC, 1, false>(F2, F0, tb.eSc, nbl);
-    __syncthreads();
+    sweep<T, 0, N, N, N, QC, 1, false>(su, F1, tb.eSc, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QC, N, N, QC, 1, false>(F1, F2, tb.eSc, nbl, grp);
+    grp.sync();
+    sweep<T, 2, QC, QC, N, QC, 1, false>(F2, F0, tb.eSc, nbl, grp);
+    grp.sync();
     // pointwise: contravariant flux  -F_c J^{-T} |J| w  (minus sign of the weak form)
-    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+    for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
       const int e = idx / P, p = idx - e * P;
       const int q0 = p % QC, q1 = (p / QC) % QC, q2 = p / (QC * QC);
       const T w = tb.wc[q0] * tb.wc[q1] * tb.wc[q2] * detJ;
@@ -294,21 +388,21 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
             Fd[b][(e * 5 + c) * P + p] = jw * (Ji[3 * b] * F[0][c] + Ji[3 * b + 1] * F[1][c] + Ji[3 * b + 2] * F[2][c]);
       }
     }
-    __syncthreads();
+    grp.sync();
     // G = sum_d D_d^T Ft_d  (test with grad V in the collocation basis)
-    sweep<T, 0, QC, QC, QC, QC, -1, false>(F0, G, tb.eDcT, nbl);
-    __syncthreads();
-    sweep<T, 1, QC, QC, QC, QC, -1, true>(F1, G, tb.eDcT, nbl);
-    __syncthreads();
-    sweep<T, 2, QC, QC, QC, QC, -1, true>(F2, G, tb.eDcT, nbl);
-    __syncthreads();
+    sweep<T, 0, QC, QC, QC, QC, -1, false>(F0, G, tb.eDcT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QC, QC, QC, QC, -1, true>(F1, G, tb.eDcT, nbl, grp);
+    grp.sync();
+    sweep<T, 2, QC, QC, QC, QC, -1, true>(F2, G, tb.eDcT, nbl, grp);
+    grp.sync();
     // back to the nodes: S^T along z, y, x
-    sweep<T, 2, QC, QC, QC, N, 1, false>(G, F0, tb.eScT, nbl);
-    __syncthreads();
-    sweep<T, 1, QC, QC, N, N, 1, false>(F0, F1, tb.eScT, nbl);
-    __syncthreads();
-    sweep<T, 0, QC, N, N, N, 1, true>(F1, sr, tb.eScT, nbl);
-    __syncthreads();
+    sweep<T, 2, QC, QC, QC, N, 1, false>(G, F0, tb.eScT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QC, QC, N, N, 1, false>(F0, F1, tb.eScT, nbl, grp);
+    grp.sync();
+    sweep<T, 0, QC, N, N, N, 1, true>(F1, sr, tb.eScT, nbl, grp);
+    grp.sync();
   }
   if (kp.visc) {
     constexpr int P = QV * QV * QV;
@@ -316,18 +410,18 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
     T* V1 = ar + CB * 5 * P;
     T* V2 = ar + 2 * CB * 5 * P;
     T* V3 = ar + 3 * CB * 5 * P;
-    sweep<T, 0, N, N, N, QV, 1, false>(su, V1, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, N, N, QV, 1, false>(V1, V2, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 2, QV, QV, N, QV, 1, false>(V2, V0, tb.eSv, nbl);
-    __syncthreads();
+    sweep<T, 0, N, N, N, QV, 1, false>(su, V1, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, N, N, QV, 1, false>(V1, V2, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 2, QV, QV, N, QV, 1, false>(V2, V0, tb.eSv, nbl, grp);
+    grp.sync();
     // reference gradients by collocation
-    sweep<T, 0, QV, QV, QV, QV, -1, false>(V0, V1, tb.eDv, nbl);
-    sweep<T, 1, QV, QV, QV, QV, -1, false>(V0, V2, tb.eDv, nbl);
-    sweep<T, 2, QV, QV, QV, QV, -1, false>(V0, V3, tb.eDv, nbl);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+    sweep<T, 0, QV, QV, QV, QV, -1, false>(V0, V1, tb.eDv, nbl, grp);
+    sweep<T, 1, QV, QV, QV, QV, -1, false>(V0, V2, tb.eDv, nbl, grp);
+    sweep<T, 2, QV, QV, QV, QV, -1, false>(V0, V3, tb.eDv, nbl, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
       const int e = idx / P, p = idx - e * P;
       const int q0 = p % QV, q1 = (p / QV) % QV, q2 = p / (QV * QV);
       const T w = tb.wv[q0] * tb.wv[q1] * tb.wv[q2] * detJ;
@@ -368,19 +462,19 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
             Vd[b][(e * 5 + c) * P + p] = jw * (Ji[3 * b] * F[c][0] + Ji[3 * b + 1] * F[c][1] + Ji[3 * b + 2] * F[c][2]);
       }
     }
-    __syncthreads();
-    sweep<T, 0, QV, QV, QV, QV, -1, false>(V1, V0, tb.eDvT, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, QV, QV, QV, -1, true>(V2, V0, tb.eDvT, nbl);
-    __syncthreads();
-    sweep<T, 2, QV, QV, QV, QV, -1, true>(V3, V0, tb.eDvT, nbl);
-    __syncthreads();
-    sweep<T, 2, QV, QV, QV, N, 1, false>(V0, V1, tb.eSvT, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, QV, N, N, 1, false>(V1, V2, tb.eSvT, nbl);
-    __syncthreads();
-    sweep<T, 0, QV, N, N, N, 1, true>(V2, sr, tb.eSvT, nbl);
-    __syncthreads();
+    grp.sync();
+    sweep<T, 0, QV, QV, QV, QV, -1, false>(V1, V0, tb.eDvT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, QV, QV, QV, -1, true>(V2, V0, tb.eDvT, nbl, grp);
+    grp.sync();
+    sweep<T, 2, QV, QV, QV, QV, -1, true>(V3, V0, tb.eDvT, nbl, grp);
+    grp.sync();
+    sweep<T, 2, QV, QV, QV, N, 1, false>(V0, V1, tb.eSvT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, QV, N, N, 1, false>(V1, V2, tb.eSvT, nbl, grp);
+    grp.sync();
+    sweep<T, 0, QV, N, N, N, 1, true>(V2, sr, tb.eSvT, nbl, grp);
+    grp.sync();
   }
 }
 
@@ -393,14 +487,16 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
 // su: own nodal state, sn: neighbour nodal state (unused where wall[e]),
 // tau_f[e]: face penalty, sr: accumulated residual, fa: face arena.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, int d, int GEO>
+template <typename T, int N, int QC, int QV, int CB, int d, int GEO, class G = CtaGroup>
 __device__ void face_terms(const T* su, const T* sn, const int* wall, const int* nbi, const T* tau_f, T* sr, T* fa,
-                           const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int e0, int nb, int s) {
+                           const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int e0, int nb, int s,
+                           G grp = G()) {
   const int f = 2 * d + s, fo = 2 * d + (1 - s);  // own face, neighbour's face
   constexpr int N2 = N * N, N3 = N * N * N;
   constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  const T hinv[3] = {T(1.0 / kp.h[0]), T(1.0 / kp.h[1]), T(1.0 / kp.h[2])};
-  const T area = T(kp.h[t1] * kp.h[t2]);
+  const KConst<T>& kc = kconst<T>(kp);
+  const T hinv[3] = {kc.hinv[0], kc.hinv[1], kc.hinv[2]};
+  const T area = kc.area[d];
   const T sgn = s ? T(1) : T(-1);  // outward unit normal n = sgn e_d
   const int idm = s ? N - 1 : 0, idp = s ? 0 : N - 1;
   const T* dlm = s ? tb.dl1 : tb.dl0;  // l_i' at the own face
@@ -414,21 +510,21 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
     T* Tm = Lp + CB * 5 * N2;     // tmp [CB][5][N][QC]
     T* Um = Tm + CB * 5 * QC * N; // [CB][5][P]
     T* Up = Um + CB * 5 * P;
-    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
       const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
       Lm[idx] = su[ec * N3 + face_node<N>(d, idm, j % N, j / N)];
       Lp[idx] = wall[e] ? T(0) : sn[ec * N3 + face_node<N>(d, idp, j % N, j / N)];
     }
-    __syncthreads();
-    sweep<T, 0, N, N, 1, QC, 1, false>(Lm, Tm, tb.eSc, nbl);
-    __syncthreads();
-    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Um, tb.eSc, nbl);
-    __syncthreads();
-    sweep<T, 0, N, N, 1, QC, 1, false>(Lp, Tm, tb.eSc, nbl);
-    __syncthreads();
-    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Up, tb.eSc, nbl);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+    grp.sync();
+    sweep<T, 0, N, N, 1, QC, 1, false>(Lm, Tm, tb.eSc, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Um, tb.eSc, nbl, grp);
+    grp.sync();
+    sweep<T, 0, N, N, 1, QC, 1, false>(Lp, Tm, tb.eSc, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QC, N, 1, QC, 1, false>(Tm, Up, tb.eSc, nbl, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
       const int e = idx / P, p = idx - e * P;
       const T w = tb.wc[p % QC] * tb.wc[p / QC] * area;
       T um[5], up[5];
@@ -470,16 +566,16 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         for (int c = 0; c < 5; ++c) Um[(e * 5 + c) * P + p] = dw * (T(0.5) * fn[c] + T(0.5) * lam * (um[c] - up[c]));
       }
     }
-    __syncthreads();
-    sweep<T, 1, QC, QC, 1, N, 1, false>(Um, Tm, tb.eScT, nbl);
-    __syncthreads();
-    sweep<T, 0, QC, N, 1, N, 1, false>(Tm, Lm, tb.eScT, nbl);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+    grp.sync();
+    sweep<T, 1, QC, QC, 1, N, 1, false>(Um, Tm, tb.eScT, nbl, grp);
+    grp.sync();
+    sweep<T, 0, QC, N, 1, N, 1, false>(Tm, Lm, tb.eScT, nbl, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
       const int ec = idx / N2, j = idx - ec * N2;
       sr[ec * N3 + face_node<N>(d, idm, j % N, j / N)] += Lm[idx];
     }
-    __syncthreads();
+    grp.sync();
   }
 
   if (kp.visc) {
@@ -497,7 +593,7 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
     T* G1p = Gdm + CB * 5 * P;
     T* G2p = G1p + CB * 5 * P;
     T* Gdp = G2p + CB * 5 * P;
-    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
       const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
       const int j1 = j % N, j2 = j / N;
       const T* um = su + ec * N3;
@@ -518,30 +614,30 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         Dp[idx] = dp;
       }
     }
-    __syncthreads();
+    grp.sync();
     // values and normal derivatives to the face Gauss points
-    sweep<T, 0, N, N, 1, QV, 1, false>(Lm, Tm, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Um, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 0, N, N, 1, QV, 1, false>(Lp, Tm, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Up, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 0, N, N, 1, QV, 1, false>(Dm, Tm, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdm, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 0, N, N, 1, QV, 1, false>(Dp, Tm, tb.eSv, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdp, tb.eSv, nbl);
+    sweep<T, 0, N, N, 1, QV, 1, false>(Lm, Tm, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Um, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 0, N, N, 1, QV, 1, false>(Lp, Tm, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Up, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 0, N, N, 1, QV, 1, false>(Dm, Tm, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdm, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 0, N, N, 1, QV, 1, false>(Dp, Tm, tb.eSv, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, N, 1, QV, 1, false>(Tm, Gdp, tb.eSv, nbl, grp);
     // tangential derivatives by collocation on the face grid
-    sweep<T, 0, QV, QV, 1, QV, -1, false>(Um, G1m, tb.eDv, nbl);
-    sweep<T, 1, QV, QV, 1, QV, -1, false>(Um, G2m, tb.eDv, nbl);
-    sweep<T, 0, QV, QV, 1, QV, -1, false>(Up, G1p, tb.eDv, nbl);
-    sweep<T, 1, QV, QV, 1, QV, -1, false>(Up, G2p, tb.eDv, nbl);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * P; idx += blockDim.x) {
+    sweep<T, 0, QV, QV, 1, QV, -1, false>(Um, G1m, tb.eDv, nbl, grp);
+    sweep<T, 1, QV, QV, 1, QV, -1, false>(Um, G2m, tb.eDv, nbl, grp);
+    sweep<T, 0, QV, QV, 1, QV, -1, false>(Up, G1p, tb.eDv, nbl, grp);
+    sweep<T, 1, QV, QV, 1, QV, -1, false>(Up, G2p, tb.eDv, nbl, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
       const int e = idx / P, p = idx - e * P;
       const T w = tb.wv[p % QV] * tb.wv[p / QV] * area;
       const int o = e * 5 * P + p;
@@ -636,22 +732,22 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         }
       }
     }
-    __syncthreads();
+    grp.sync();
     // value test + tangential gradient tests on the face grid
-    sweep<T, 0, QV, QV, 1, QV, -1, true>(G1m, Um, tb.eDvT, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, QV, 1, QV, -1, true>(G2m, Um, tb.eDvT, nbl);
-    __syncthreads();
-    sweep<T, 1, QV, QV, 1, N, 1, false>(Um, Tm, tb.eSvT, nbl);
-    __syncthreads();
-    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Lm, tb.eSvT, nbl);
-    __syncthreads();
+    sweep<T, 0, QV, QV, 1, QV, -1, true>(G1m, Um, tb.eDvT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, QV, 1, QV, -1, true>(G2m, Um, tb.eDvT, nbl, grp);
+    grp.sync();
+    sweep<T, 1, QV, QV, 1, N, 1, false>(Um, Tm, tb.eSvT, nbl, grp);
+    grp.sync();
+    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Lm, tb.eSvT, nbl, grp);
+    grp.sync();
     // normal gradient test
-    sweep<T, 1, QV, QV, 1, N, 1, false>(Gdm, Tm, tb.eSvT, nbl);
-    __syncthreads();
-    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Dm, tb.eSvT, nbl);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nbl * N2; idx += blockDim.x) {
+    sweep<T, 1, QV, QV, 1, N, 1, false>(Gdm, Tm, tb.eSvT, nbl, grp);
+    grp.sync();
+    sweep<T, 0, QV, N, 1, N, 1, false>(Tm, Dm, tb.eSvT, nbl, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
       const int ec = idx / N2, j = idx - ec * N2;
       const int j1 = j % N, j2 = j / N;
       const T lv = Lm[idx], dv = Dm[idx];
@@ -663,7 +759,7 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         r[face_node<N>(d, i, j1, j2)] += add;
       }
     }
-    __syncthreads();
+    grp.sync();
   }
 }
 
@@ -674,22 +770,22 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
 // S^{-1} F_rhs(x_q) (nodal coefficients of its Gauss-point interpolant).
 // su is needed only for the body force (u at the mass points).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int CB, int GEO>
+template <typename T, int N, int CB, int GEO, class G = CtaGroup>
 __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int e0, int nb,
-                             bool negate, bool add_force) {
+                             bool negate, bool add_force, G grp = G()) {
   constexpr int N3 = N * N * N;
   const int nbl = nb * 5;
   T* A = ma;
   T* B = ma + CB * 5 * N3;
-  const T detJ = T(kp.h[0] * kp.h[1] * kp.h[2]);
-  sweep<T, 0, N, N, N, N, 1, false>(sr, A, tb.eSmiT, nbl);
-  __syncthreads();
-  sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmiT, nbl);
-  __syncthreads();
-  sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmiT, nbl);
-  __syncthreads();
+  const T detJ = kconst<T>(kp).detJ;
+  sweep<T, 0, N, N, N, N, 1, false>(sr, A, tb.eSmiT, nbl, grp);
+  grp.sync();
+  sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmiT, nbl, grp);
+  grp.sync();
+  sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmiT, nbl, grp);
+  grp.sync();
   const T sg = negate ? T(-1) : T(1);
-  for (int idx = threadIdx.x; idx < nbl * N3; idx += blockDim.x) {
+  for (int idx = grp.rank(); idx < nbl * N3; idx += grp.size()) {
     const int p = idx % N3;
     T w;
     if (GEO == GEO_AFFINE)
@@ -699,38 +795,38 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
           static_cast<const T*>(kp.gm)[(size_t)(e0 + idx / (5 * N3)) * N3 + p];
     A[idx] *= sg / w;
   }
-  __syncthreads();
-  sweep<T, 0, N, N, N, N, 1, false>(A, B, tb.eSmi, nbl);
-  __syncthreads();
-  sweep<T, 1, N, N, N, N, 1, false>(B, A, tb.eSmi, nbl);
-  __syncthreads();
-  sweep<T, 2, N, N, N, N, 1, false>(A, sr, tb.eSmi, nbl);
-  __syncthreads();
+  grp.sync();
+  sweep<T, 0, N, N, N, N, 1, false>(A, B, tb.eSmi, nbl, grp);
+  grp.sync();
+  sweep<T, 1, N, N, N, N, 1, false>(B, A, tb.eSmi, nbl, grp);
+  grp.sync();
+  sweep<T, 2, N, N, N, N, 1, false>(A, sr, tb.eSmi, nbl, grp);
+  grp.sync();
   if (add_force) {
     // F_rhs = (0, f, f.u): momentum rows are the constant f (S^{-1} 1 = 1), energy row S^{-1}(f . u)(x_q)
-    const T f0 = T(kp.bf[0]), f1 = T(kp.bf[1]), f2 = T(kp.bf[2]);
+    const T f0 = kconst<T>(kp).bf[0], f1 = kconst<T>(kp).bf[1], f2 = kconst<T>(kp).bf[2];
     // interpolate rho and momenta (components 0..3) to the mass points
     for (int e = 0; e < nb; ++e) {
-      sweep<T, 0, N, N, N, N, 1, false>(su + e * 5 * N3, A + e * 4 * N3, tb.eSm, 4);
+      sweep<T, 0, N, N, N, N, 1, false>(su + e * 5 * N3, A + e * 4 * N3, tb.eSm, 4, grp);
     }
-    __syncthreads();
-    for (int e = 0; e < nb; ++e) sweep<T, 1, N, N, N, N, 1, false>(A + e * 4 * N3, B + e * 4 * N3, tb.eSm, 4);
-    __syncthreads();
-    for (int e = 0; e < nb; ++e) sweep<T, 2, N, N, N, N, 1, false>(B + e * 4 * N3, A + e * 4 * N3, tb.eSm, 4);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
+    grp.sync();
+    for (int e = 0; e < nb; ++e) sweep<T, 1, N, N, N, N, 1, false>(A + e * 4 * N3, B + e * 4 * N3, tb.eSm, 4, grp);
+    grp.sync();
+    for (int e = 0; e < nb; ++e) sweep<T, 2, N, N, N, N, 1, false>(B + e * 4 * N3, A + e * 4 * N3, tb.eSm, 4, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nb * N3; idx += grp.size()) {
       const int e = idx / N3, p = idx - e * N3;
       const T* a = A + e * 4 * N3;
-      B[idx] = (f0 * a[N3 + p] + f1 * a[2 * N3 + p] + f2 * a[3 * N3 + p]) / (T(kp.rho_ref) + a[p]);
+      B[idx] = (f0 * a[N3 + p] + f1 * a[2 * N3 + p] + f2 * a[3 * N3 + p]) / (kconst<T>(kp).rho_r + a[p]);
     }
-    __syncthreads();
-    sweep<T, 0, N, N, N, N, 1, false>(B, A, tb.eSmi, nb);
-    __syncthreads();
-    sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmi, nb);
-    __syncthreads();
-    sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmi, nb);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * N3; idx += blockDim.x) {
+    grp.sync();
+    sweep<T, 0, N, N, N, N, 1, false>(B, A, tb.eSmi, nb, grp);
+    grp.sync();
+    sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmi, nb, grp);
+    grp.sync();
+    sweep<T, 2, N, N, N, N, 1, false>(B, A, tb.eSmi, nb, grp);
+    grp.sync();
+    for (int idx = grp.rank(); idx < nb * N3; idx += grp.size()) {
       const int e = idx / N3, p = idx - e * N3;
       T* r = sr + e * 5 * N3;
       r[N3 + p] += f0;
@@ -738,7 +834,7 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
       r[3 * N3 + p] += f2;
       r[4 * N3 + p] += A[idx];
     }
-    __syncthreads();
+    grp.sync();
   }
 }
 

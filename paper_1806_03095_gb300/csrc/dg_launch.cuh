@@ -10,15 +10,32 @@
 namespace dgcns {
 
 
-// Cells per CTA: the largest batch (<= 8) whose shared memory stays below ~112 KB,
-// so that two CTAs fit on one SM (228 KB).
+// Cells per CTA: the largest batch (<= 4 for FP32, <= 8 for FP64) whose shared
+// memory stays below ~112 KB, so that two or more CTAs fit on one SM (228 KB).
 template <typename T, int N, int QC, int QV>
 constexpr int cells_per_cta() {
   using S = Sizes<N, QC, QV>;
   constexpr int arena = S::CELL_ARENA > S::FACE_ARENA ? S::CELL_ARENA : S::FACE_ARENA;
   constexpr int per_cell = (3 * 5 * S::N3 + arena) * (int)sizeof(T) + 8;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_cell;
-  return cb < 1 ? 1 : (cb > 8 ? 8 : cb);
+  constexpr int cap = sizeof(T) == 4 ? 4 : 8;
+  return cb < 1 ? 1 : (cb > cap ? cap : cb);
+}
+
+// Threads per CTA of the operator kernel: the FP32 form needs more warps per SM to
+// hide latency (its FMA pipe is 64x wider than the FP64 one).
+template <typename T>
+constexpr int op_threads() {
+  return sizeof(T) == 4 ? 256 : 128;
+}
+
+// Deviation state U - U_ref in the arithmetic type (elementwise pre-pass of the mixed form).
+template <typename T>
+__global__ void dg_dev_kernel(const KParams kp, const double* __restrict__ U, T* __restrict__ D, size_t n, int N3) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)((i / N3) % 5);
+    D[i] = T(U[i] - (c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0)));
+  }
 }
 
 template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS>
@@ -44,7 +61,7 @@ __device__ __forceinline__ double ref_of(const KParams& kp, int c) {
 // dU <- A dU + dt L, U_out <- U + B dU.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
-__global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const double* __restrict__ U,
+__global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp, const double* __restrict__ U,
                                                    const T* Rin, T* Rout, T* dU, double* Uout) {
   using S = Sizes<N, QC, QV>;
   constexpr int N3 = S::N3;
@@ -67,22 +84,14 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
   const int nb = min(CB, kp.Nc - e0);
   if (nb <= 0) return;
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
-  PhysT<T> ph;
-  ph.gamma = T(kp.gamma);
-  ph.gm1 = T(kp.gamma - 1.0);
-  ph.mu = T(kp.mu);
-  ph.lam_cv = T(kp.lam / kp.cv);
-  ph.rho_r = T(kp.rho_ref);
-  ph.rhoE_r = T(kp.rhoE_ref);
-  ph.p_r = T((kp.gamma - 1.0) * kp.rhoE_ref);
-  ph.H_r = T(kp.gamma * kp.rhoE_ref);
-  ph.cvTw2 = T(2.0 * kp.cv * kp.Tw);
+  const PhysT<T> ph = make_phys<T>(kp);
 
   const size_t base = (size_t)e0 * 5 * N3;
   const int nvals = nb * 5 * N3;
   const bool need_u = CELL || FACE || (MASS && kp.has_bf);
+  const T* Ud = static_cast<const T*>(kp.Udev);
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    if (need_u) su[i] = T(U[base + i] - ref_of(kp, (i / N3) % 5));
+    if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
     sr[i] = CELL ? T(0) : Rin[base + i];
   }
   __syncthreads();
@@ -112,7 +121,10 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
         __syncthreads();
         for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
           const int e = i / (5 * N3);
-          if (!wall[e]) sn[i] = T(U[(size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3)] - ref_of(kp, (i / N3) % 5));
+          if (!wall[e]) {
+            const size_t src = (size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3);
+            sn[i] = Ud ? Ud[src] : T(U[src] - ref_of(kp, (i / N3) % 5));
+          }
         }
         __syncthreads();
         if (d == 0) face_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
@@ -126,10 +138,11 @@ __global__ void __launch_bounds__(NT) dg_op_kernel(const KParams kp, const doubl
     inverse_mass<T, N, CB, GEO>(su, sr, ar, tb, kp, e0, nb, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0);
 
   if (kp.out_mode == 2) {
-    const double A = kp.A, B = kp.B, dt = kp.dt;
+    // 2N update: dU in the residual type, the state accumulated in FP64
+    const T A = T(kp.A), dt = T(kp.dt);
+    const double B = kp.B;
     for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-      const double du_old = A != 0.0 ? double(dU[base + i]) : 0.0;
-      const T du = T(A * du_old + dt * double(sr[i]));
+      const T du = (kp.A != 0.0 ? A * dU[base + i] : T(0)) + dt * sr[i];
       dU[base + i] = du;
       Uout[base + i] = U[base + i] + B * double(du);
     }
@@ -612,7 +625,134 @@ int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, v
     attr = true;
   }
   const int grid = (kp.Nc + CB - 1) / CB;
-  k<<<grid, NT, smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout), static_cast<T*>(dU), Uout);
+  k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout),
+                                          static_cast<T*>(dU), Uout);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-cell organisation of the same operator (used for the FP32 form):
+// WPC warps per CTA, each warp carries one cell through all phases with
+// warp-level barriers only, so the warps of an SM progress independently and
+// hide each other's latency.  Shared memory: the tables (per CTA) and one
+// private slice per warp.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int QC, int QV, bool CELL, bool FACE, bool MASS>
+constexpr int warp_slice_elems() {
+  using S = Sizes<N, QC, QV>;
+  int arena = 0;
+  if (CELL) arena = S::CELL_ARENA;
+  if (FACE && S::FACE_ARENA > arena) arena = S::FACE_ARENA;
+  if (MASS && S::MASS_ARENA > arena) arena = S::MASS_ARENA;
+  const int e = 5 * S::N3 * (FACE ? 3 : 2) + arena + 1 + 2 * 8 / (int)sizeof(T) + 2;
+  return (e + 7) & ~7;
+}
+
+template <typename T, int N, int QC, int QV, int WPC, bool CELL, bool FACE, bool MASS>
+constexpr size_t warp_smem_bytes() {
+  return ((size_t)table_elems<N, QC, QV>() + (size_t)WPC * warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS>()) *
+             sizeof(T) + 64;
+}
+
+template <typename T, int N, int QC, int QV, int WPC, bool CELL, bool FACE, bool MASS, int GEO>
+__global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, const double* __restrict__ U,
+                                                              const T* Rin, T* Rout, T* dU, double* Uout) {
+  using S = Sizes<N, QC, QV>;
+  constexpr int N3 = S::N3;
+  constexpr int SL = warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* stab = sm;
+  const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  const int e0 = blockIdx.x * WPC + w;
+  if (e0 >= kp.Nc) return;  // only warp barriers below
+  const WarpGroup grp;
+  T* su = stab + table_elems<N, QC, QV>() + w * SL;
+  T* sr = su + 5 * N3;
+  T* sn = sr + 5 * N3;
+  T* ar = sn + (FACE ? 5 * N3 : 0);
+  int arena = 0;
+  if (CELL) arena = S::CELL_ARENA;
+  if (FACE && S::FACE_ARENA > arena) arena = S::FACE_ARENA;
+  if (MASS && S::MASS_ARENA > arena) arena = S::MASS_ARENA;
+  T* tau_f = ar + arena;
+  int* wall = reinterpret_cast<int*>(su + SL) - 2;  // two ints at the end of the slice
+  int* nbi = wall + 1;
+  const PhysT<T> ph = make_phys<T>(kp);
+  const size_t base = (size_t)e0 * 5 * N3;
+  constexpr int nvals = 5 * N3;
+  const bool need_u = CELL || FACE || (MASS && kp.has_bf);
+  const T* Ud = static_cast<const T*>(kp.Udev);
+  for (int i = grp.rank(); i < nvals; i += 32) {
+    if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
+    sr[i] = CELL ? T(0) : Rin[base + i];
+  }
+  grp.sync();
+  if (CELL) cell_terms<T, N, QC, QV, 1, GEO>(su, sr, ar, tb, kp, ph, e0, 1, grp);
+  if (FACE) {
+    for (int d = 0; d < 3; ++d) {
+      for (int s = 0; s < 2; ++s) {
+        if (grp.rank() == 0) {
+          int c[3] = {e0 % kp.nc[0], (e0 / kp.nc[0]) % kp.nc[1], e0 / (kp.nc[0] * kp.nc[1])};
+          c[d] += s ? 1 : -1;
+          int wl = 0;
+          if (c[d] < 0 || c[d] >= kp.nc[d]) {
+            if (kp.periodic[d])
+              c[d] = (c[d] + kp.nc[d]) % kp.nc[d];
+            else
+              wl = 1;
+          }
+          const int en = wl ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+          nbi[0] = en;
+          wall[0] = wl;
+          const double te = kp.tau[e0];
+          tau_f[0] = T(wl ? te : fmax(te, kp.tau[en]));
+        }
+        grp.sync();
+        if (!wall[0]) {
+          const size_t nb0 = (size_t)nbi[0] * 5 * N3;
+          for (int i = grp.rank(); i < nvals; i += 32)
+            sn[i] = Ud ? Ud[nb0 + i] : T(U[nb0 + i] - ref_of(kp, (i / N3) % 5));
+        }
+        grp.sync();
+        if (d == 0) face_terms<T, N, QC, QV, 1, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
+        if (d == 1) face_terms<T, N, QC, QV, 1, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
+        if (d == 2) face_terms<T, N, QC, QV, 1, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
+      }
+    }
+  }
+  if (MASS)
+    inverse_mass<T, N, 1, GEO>(su, sr, ar, tb, kp, e0, 1, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0, grp);
+  if (kp.out_mode == 2) {
+    const T A = T(kp.A), dt = T(kp.dt);
+    const double B = kp.B;
+    for (int i = grp.rank(); i < nvals; i += 32) {
+      const T du = (kp.A != 0.0 ? A * dU[base + i] : T(0)) + dt * sr[i];
+      dU[base + i] = du;
+      Uout[base + i] = U[base + i] + B * double(du);
+    }
+  } else {
+    for (int i = grp.rank(); i < nvals; i += 32) Rout[base + i] = sr[i];
+  }
+}
+
+template <typename T, int N, int QC, int QV, bool CELL, bool FACE, bool MASS, int GEO>
+int launch_op_warp(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
+                   cudaStream_t st) {
+  constexpr int WPC = 4;
+  constexpr size_t smem = warp_smem_bytes<T, N, QC, QV, WPC, CELL, FACE, MASS>();
+  if (smem > 227 * 1024) return -2;
+  auto k = dg_op_warp_kernel<T, N, QC, QV, WPC, CELL, FACE, MASS, GEO>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    attr = true;
+  }
+  const int grid = (kp.Nc + WPC - 1) / WPC;
+  k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout), static_cast<T*>(dU),
+                                    Uout);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -620,14 +760,24 @@ template <typename T, int N, int QC, int QV, int GEO>
 int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU,
                     double* Uout, cudaStream_t st) {
   constexpr int CB = cells_per_cta<T, N, QC, QV>();
+  // FP32: warp per cell (latency-bound otherwise); FP64: CTA per cell batch (FP64-pipe bound)
+  constexpr bool WARP = sizeof(T) == 4 && warp_smem_bytes<T, N, QC, QV, 4, true, true, true>() <= 227 * 1024;
   switch (mode) {
-    case OP_CELL: return launch_op<T, N, QC, QV, CB, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_FACE: return launch_op<T, N, QC, QV, CB, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_MASS: return launch_op<T, N, QC, QV, CB, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_CELL:
+      return WARP ? launch_op_warp<T, N, QC, QV, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
+                  : launch_op<T, N, QC, QV, CB, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_FACE:
+      return WARP ? launch_op_warp<T, N, QC, QV, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
+                  : launch_op<T, N, QC, QV, CB, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_MASS:
+      return WARP ? launch_op_warp<T, N, QC, QV, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st)
+                  : launch_op<T, N, QC, QV, CB, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_FACE:
-      return launch_op<T, N, QC, QV, CB, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+      return WARP ? launch_op_warp<T, N, QC, QV, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
+                  : launch_op<T, N, QC, QV, CB, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_FACE | OP_MASS:
-      return launch_op<T, N, QC, QV, CB, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+      return WARP ? launch_op_warp<T, N, QC, QV, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st)
+                  : launch_op<T, N, QC, QV, CB, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
     default: return -2;
   }
 }
@@ -665,6 +815,13 @@ int diag_launch(const KParams& kp, const double* U, const void* LU, double* part
   return diag_launch_geo<TL, N, QC, QV, GEO_STORED>(kp, U, LU, partial, nblocks, st);
 }
 
+template <typename T, int N>
+int dev_launch(const KParams& kp, const double* U, void* D, cudaStream_t st) {
+  const size_t n = (size_t)kp.Nc * 5 * N * N * N;
+  dg_dev_kernel<T><<<2 * 152 * 8, 256, 0, st>>>(kp, U, static_cast<T*>(D), n, N * N * N);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int N, int QC, int QV>
 Launchers make_launchers() {
   Launchers L;
@@ -678,6 +835,7 @@ Launchers make_launchers() {
   L.prep_fp64 = adj_prep_launch<double>;
   L.prep_fp32 = adj_prep_launch<float>;
   L.ekgrad = ekgrad_launch<N, QC, QV>;
+  L.dev_fp32 = dev_launch<float, N>;
   L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
   L.cb_fp32 = cells_per_cta<float, N, QC, QV>();
   return L;

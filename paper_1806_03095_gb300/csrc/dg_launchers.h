@@ -30,6 +30,7 @@ struct Launchers {
   AdjFn adj_fp64, adj_fp32;
   PrepFn prep_fp64, prep_fp32;
   EkGradFn ekgrad;
+  int (*dev_fp32)(const KParams&, const double* U, void* D, cudaStream_t);  // D = float(U - U_ref)
   int cb_fp64, cb_fp32;
 };
 

@@ -255,6 +255,7 @@ struct dgcns_ctx {
   float* d_tab32 = nullptr;
   double* d_tau = nullptr;
   void* d_R = nullptr;        // residual scratch (split kernels)
+  float* d_dev = nullptr;     // FP32 deviation state U - U_ref (mixed form)
   double* g64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stored geometry, FP64 (gcc gcv gfc gfv gm)
   float* g32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the mixed form
   size_t gsize[5] = {0, 0, 0, 0, 0};
@@ -420,7 +421,8 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess) {
+  if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess ||
+      (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess)) {
     cudaGetLastError();
     dg_cns_destroy(c);
     return DGCNS_ERR_OOM;
@@ -441,6 +443,8 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   kp.Tw = c->Tw;
   kp.rho_ref = prm->rho0;
   kp.rhoE_ref = prm->rho0 * c->cv * c->Tw;
+  fill_kconst(kp, kp.cd);
+  fill_kconst(kp, kp.cf);
   kp.tau = c->d_tau;
   kp.conv = kp.visc = 1;
   c->volume = (mesh->hi[0] - mesh->lo[0]) * (mesh->hi[1] - mesh->lo[1]) * (mesh->hi[2] - mesh->lo[2]);
@@ -555,6 +559,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_tab32);
   cudaFree(c->d_tau);
   cudaFree(c->d_R);
+  cudaFree(c->d_dev);
   cudaFree(c->d_partial);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
@@ -599,7 +604,19 @@ static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const voi
 }
 
 // L(U) into dst (mode 1) or a stage update (mode 2) with the configured kernel organisation.
+// The mixed form reads own and neighbour states as FP32 deviations U - U_ref: convert U once per
+// operator evaluation (an elementwise pass) so that the operator kernels do no FP64 conversions.
+static int prep_dev(dgcns_ctx* c, KParams& kp, const double* U) {
+  if (!c->d_dev || !U) return DGCNS_OK;
+  if (c->L.dev_fp32(kp, U, c->d_dev, c->stream) != 0) return cuda_fail(c, "deviation pre-pass");
+  c->launches += 1;
+  kp.Udev = c->d_dev;
+  return DGCNS_OK;
+}
+
 static int eval_L(dgcns_ctx* c, KParams kp, const double* U, void* dst, void* dU, double* Uout) {
+  const int rd = prep_dev(c, kp, U);
+  if (rd) return rd;
   if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE | OP_MASS, kp, U, nullptr, dst, dU, Uout);
   KParams k0 = kp;
   k0.out_mode = 0;
@@ -625,6 +642,8 @@ int dg_cns_apply(dgcns_ctx* c, const double* U, void* R, int op) {
       kp.out_mode = 0;
       kp.conv = op != DGCNS_OP_FV;
       kp.visc = op != DGCNS_OP_FC;
+      const int rd = prep_dev(c, kp, U);
+      if (rd) return rd;
       if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE, kp, U, nullptr, R, nullptr, nullptr);
       int r = run_op(c, OP_CELL, kp, U, nullptr, R, nullptr, nullptr);
       if (r) return r;
