@@ -152,6 +152,9 @@ def time_native(cfg, steps, warmup, device):
     return ctx, bufs, dt, ms, launches
 
 
+KERNELS = {"split": 0, "fused": 1, "faces": 2}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,7 +163,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="tgv64_k3")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--kernel", choices=["fused", "split"], default="fused")
+    ap.add_argument("--kernel", choices=["fused", "split", "faces"], default="fused")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -174,7 +177,7 @@ def main():
         raise RuntimeError("bench.py native arm needs a GPU")
     torch.cuda.set_device(device)
     prec = 1 if args.precision == "mixed" else 0
-    cfg = configs.WORKLOADS[args.workload](precision=prec, kernel=1 if args.kernel == "fused" else 0)
+    cfg = configs.WORKLOADS[args.workload](precision=prec, kernel=KERNELS[args.kernel])
     N = cfg["k"] + 1
     Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
     nodes = Nc * N ** 3
@@ -263,7 +266,8 @@ def extras(args, cfg):
     res = {}
     device = torch.cuda.current_device()
     steps = max(2, args.steps // 2)
-    for name, prec, kern in (("fp64_split", 0, 0), ("mixed_fused", 1, 1), ("mixed_split", 1, 0)):
+    for name, prec, kern in (("fp64_split", 0, 0), ("fp64_faces", 0, 2), ("mixed_fused", 1, 1), ("mixed_split", 1, 0),
+                             ("mixed_faces", 1, 2)):
         c = dict(cfg, precision=prec, kernel=kern)
         ctx, bufs, dt, ms, _ = time_native(c, steps, 3, device)
         nodes = bufs[0].numel() // 5
@@ -283,7 +287,81 @@ def extras(args, cfg):
     del g64, g32, U, L64, L32, d
     torch.cuda.empty_cache()
     res["adjoint"] = adjoint_cost()
+    res.update(other_workloads(steps))
+    res["mixed_dissipation_history"] = dissipation_history()
     return res
+
+
+def _rate(ms, nodes, steps):
+    return round(5 * nodes * 5 * steps / (ms * 1e-3) / 1e9, 4)
+
+
+def other_workloads(steps):
+    """Throughput of the other benchmark workloads: TGV 40^3 k=5 (FP64 and mixed, fused) with the mixed form's
+    error of L(U); the turbulent channel 32^3 k=3 on the stretched mesh (walls, body force), mixed and FP64, with the
+    Jacobians stored per point and recomputed in the kernels from the node coordinates."""
+    from paper_1806_03095_gb300 import api, configs, inputs
+    device = torch.cuda.current_device()
+    out = {}
+    for key, wl, prec, geo in (("tgv40_k5_fp64", "tgv40_k5", 0, 0), ("tgv40_k5_mixed", "tgv40_k5", 1, 0),
+                               ("channel32_k3_mixed", "channel32_k3", 1, 0), ("channel32_k3_fp64", "channel32_k3", 0, 0),
+                               ("channel32_k3_mixed_geometry_on_the_fly", "channel32_k3", 1, 1),
+                               ("channel32_k3_fp64_geometry_on_the_fly", "channel32_k3", 0, 1)):
+        cfg = dict(configs.WORKLOADS[wl](precision=prec, kernel=1), geometry=geo)
+        ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+        nodes = bufs[0].numel() // 5
+        out[key] = {"value": _rate(ms, nodes, steps), "unit": UNIT, "ms_per_step": round(ms / steps, 3), "dt": dt}
+        del ctx, bufs
+        torch.cuda.empty_cache()
+    g64 = configs.make_context(configs.WORKLOADS["tgv40_k5"](precision=0), device=device)
+    g32 = configs.make_context(configs.WORKLOADS["tgv40_k5"](precision=1), device=device)
+    U = inputs.tgv_state(g64.node_coords())
+    L64 = g64.apply(U, op=api.OP_L)
+    d = g32.apply(U, op=api.OP_L).double() - L64
+    out["tgv40_k5_mixed_error_vs_fp64"] = {"quantity": "L(U) of the initial TGV state, 40^3, k=5",
+                                           "rel_l2": float(torch.linalg.norm(d) / torch.linalg.norm(L64)),
+                                           "rel_max": float(d.abs().max() / L64.abs().max())}
+    del g64, g32, U, L64, d
+    torch.cuda.empty_cache()
+    return out
+
+
+def dissipation_history(t_final=2.0, every=8):
+    """-de_k/dt over t in [0, 2] on TGV 8^3, k = 5 (the 8^3 subset of the 40^3 workload), FP64 (parity-tested
+    against the oracle) and mixed, from L(U) every `every` steps; the oracle itself anchors t = 0."""
+    from paper_1806_03095_gb300 import api, configs, inputs
+    device = torch.cuda.current_device()
+    cfg64 = configs.tgv(8, 5, precision=0)
+    hist = {}
+    for prec in (0, 1):
+        g = configs.make_context(dict(cfg64, precision=prec), device=device)
+        U = inputs.tgv_state(g.node_coords()).contiguous()
+        Ut, dU = g.empty_state(), g.empty_residual()
+        dt = configs.time_step(cfg64)
+        nsteps = int(round(t_final / dt))
+        vals = []
+        for n in range(0, nsteps + 1, every):
+            vals.append(float(g.diagnostics(U, g.apply(U, op=api.OP_L))[2]))
+            if n + every <= nsteps:
+                res = run_stages(g, every, dt, n * dt, (U, Ut, dU))
+                if res.data_ptr() != U.data_ptr():
+                    U, Ut = Ut, U
+        hist[prec] = torch.tensor(vals, dtype=torch.float64)
+        del g
+    a, b = hist[0], hist[1]
+    from oracle import diagnostics as odiag, physics as ph
+    from oracle.mesh import BoxMesh
+    from oracle.operator import DGOperator
+    mesh = BoxMesh((8, 8, 8), cfg64["lo"], cfg64["hi"], (1, 1, 1), 5)
+    op = DGOperator(mesh, ph.Physics.from_numbers(1600.0, 0.71, 0.1), cfg64["nq_conv"], cfg64["nq_visc"])
+    U0 = inputs.tgv_state(op.xyz)
+    o0 = float(odiag.diagnostics(op, U0, op.L(U0))[2])
+    return {"quantity": "-de_k/dt, TGV 8^3, k=5, t in [0, %g], sampled every %d steps (%d samples)"
+                        % (t_final, every, len(a)),
+            "rel_l2_mixed_vs_fp64": float(torch.linalg.norm(b - a) / torch.linalg.norm(a)),
+            "rel_max_mixed_vs_fp64": float((b - a).abs().max() / a.abs().max()),
+            "t0_oracle": o0, "t0_fp64": float(a[0]), "t0_mixed": float(b[0]),
+            "final_fp64": float(a[-1]), "final_mixed": float(b[-1])}
 
 
 def adjoint_cost(nsteps=200, every=20):

@@ -57,6 +57,10 @@ extern "C" {
 
 #define DGCNS_KERNEL_SPLIT 0 /* cell kernel, face kernel, inverse-mass/stage kernel */
 #define DGCNS_KERNEL_FUSED 1 /* one kernel per stage: cells, 6 faces, M^-1, update */
+/* Face-centric: a face kernel evaluates every face once and stores both cells' shares (a
+   context-owned buffer of 60 (k+1)^2 values per cell), then one kernel per stage adds cells and
+   face shares, applies M^-1 and the update. */
+#define DGCNS_KERNEL_FACES 2
 
 #define DGCNS_MAP_AFFINE 0   /* uniform Cartesian box (Sec. 4.2.1)                     */
 #define DGCNS_MAP_CHANNEL 1  /* y -> tanh(C(2 eta - 1))/tanh(C), C = map_param (Sec. 4.3.1) */
@@ -92,9 +96,15 @@ typedef struct {
   double gamma, Pr, Re, Ma, R, rho0, U0, L, u_mach;
   double body_force[3];
   int precision; /* DGCNS_FP64 or DGCNS_MIXED */
-  int kernel;    /* DGCNS_KERNEL_SPLIT or DGCNS_KERNEL_FUSED */
-  int reserved[4];
+  int kernel;    /* DGCNS_KERNEL_SPLIT, DGCNS_KERNEL_FUSED or DGCNS_KERNEL_FACES */
+  int geometry;  /* non-affine meshes: DGCNS_GEO_STORED (Jacobians stored per quadrature point, computed
+                    once in FP64) or DGCNS_GEO_ON_THE_FLY (the operator kernels recompute them from the
+                    node coordinates; diagnostics and the adjoint use the stored FP64 geometry) */
+  int reserved[3];
 } dgcns_params;
+
+#define DGCNS_GEO_STORED 0
+#define DGCNS_GEO_ON_THE_FLY 1
 
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
  * (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,

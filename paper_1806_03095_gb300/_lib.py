@@ -13,8 +13,9 @@ DGCNS_OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "OOM", -5: "NONFINITE", -6: "TIMEOUT"}
 
 FP64, MIXED = 0, 1
-KERNEL_SPLIT, KERNEL_FUSED = 0, 1
+KERNEL_SPLIT, KERNEL_FUSED, KERNEL_FACES = 0, 1, 2
 MAP_AFFINE, MAP_CHANNEL, MAP_SINE = 0, 1, 2
+GEO_STORED, GEO_ON_THE_FLY = 0, 1
 OP_L, OP_F, OP_FC, OP_FV = 0, 1, 2, 3
 NDIAG = 9
 NOALLOC_SCRATCH_BYTES = 16 << 20  # static device scratch of dg_cns_diagnostics_noalloc
@@ -37,7 +38,7 @@ class Params(ctypes.Structure):
                 ("Ma", ctypes.c_double), ("R", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("U0", ctypes.c_double), ("L", ctypes.c_double), ("u_mach", ctypes.c_double),
                 ("body_force", ctypes.c_double * 3), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("geometry", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None

@@ -1,7 +1,8 @@
 """Build libdgcns.so in-tree with nvcc for sm_103a (GB300).
 
-One translation unit per (k+1, nq_conv, nq_visc) instantiation plus the host
-file, compiled in parallel, then linked into paper_1806_03095_gb300/libdgcns.so.
+One translation unit per (k+1, nq_conv, nq_visc) instantiation and part (FP64
+operator, FP32 operator, diagnostics + geometry, adjoint) plus the host file,
+compiled in parallel, then linked into paper_1806_03095_gb300/libdgcns.so.
 Usage: python -m paper_1806_03095_gb300.build [--jobs N] [--force]
 """
 import argparse
@@ -40,6 +41,11 @@ def configs():
     return [tuple(int(v) for v in m) for m in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+)\)", block)]
 
 
+def parts():
+    text = open(os.path.join(CSRC, "dg_launchers.h")).read()
+    return int(re.search(r"#define DGCNS_PARTS (\d+)", text).group(1))
+
+
 def _sources_digest():
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
@@ -70,10 +76,11 @@ def build(jobs=None, force=False, verbose=False, extra=()):
     cmds = []
     objs = []
     for (N, QC, QV) in configs():
-        obj = os.path.join(BUILD, "inst_%d_%d_%d.o" % (N, QC, QV))
-        cmds.append([exe, *ARCH, *FLAGS, *extra, "-DINST_N=%d" % N, "-DINST_QC=%d" % QC, "-DINST_QV=%d" % QV,
-                     "-c", os.path.join(CSRC, "dg_inst.cu"), "-o", obj])
-        objs.append(obj)
+        for part in range(parts()):
+            obj = os.path.join(BUILD, "inst_%d_%d_%d_%d.o" % (N, QC, QV, part))
+            cmds.append([exe, *ARCH, *FLAGS, *extra, "-DINST_N=%d" % N, "-DINST_QC=%d" % QC, "-DINST_QV=%d" % QV,
+                         "-DINST_PART=%d" % part, "-c", os.path.join(CSRC, "dg_inst.cu"), "-o", obj])
+            objs.append(obj)
     host_obj = os.path.join(BUILD, "dgcns.o")
     cmds.append([exe, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, "dgcns.cu"), "-o", host_obj])
     objs.append(host_obj)

@@ -11,6 +11,7 @@
 // Y of the neighbour), so no two CTAs write the same cell.
 #pragma once
 #include "dg_adjoint_point.cuh"
+#include "dg_launchers.h"
 
 namespace dgcns {
 
@@ -589,8 +590,14 @@ int adj_launch_geo(const KParams& kp, const double* U, const void* Y, void* G, d
 
 template <typename T, int N, int QC, int QV>
 int adj_launch(const KParams& kp, const double* U, const void* Y, void* G, double* lamU, cudaStream_t st) {
-  if (kp.gcc == nullptr) return adj_launch_geo<T, N, QC, QV, GEO_AFFINE>(kp, U, Y, G, lamU, st);
-  return adj_launch_geo<T, N, QC, QV, GEO_STORED>(kp, U, Y, G, lamU, st);
+  using F = Feat<N, QC, QV>;
+  if constexpr (!F::adj || (sizeof(T) == 4 && !F::fp32)) {
+    return -2;
+  } else {
+    if (kp.gcc == nullptr) return adj_launch_geo<T, N, QC, QV, GEO_AFFINE>(kp, U, Y, G, lamU, st);
+    if constexpr (F::geo) return adj_launch_geo<T, N, QC, QV, GEO_STORED>(kp, U, Y, G, lamU, st);
+    return -2;
+  }
 }
 
 template <typename T>

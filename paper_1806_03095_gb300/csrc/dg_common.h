@@ -83,6 +83,11 @@ struct KParams {
   // Optional deviation state U - U_ref already converted to the kernel's precision (same layout as U);
   // when set, the operator kernels read own and neighbour values from it instead of converting U.
   const void* Udev;
+  // Node coordinates [Nc][3][N^3] in the kernel's precision (GEO_FLY: Jacobians recomputed in the kernels).
+  const void* xyzT;
+  // Face shares [Nc][6][2][5][N^2] written by the face-centric face kernel; when set, the cell kernel
+  // (without FACE) adds them to the residual.
+  const void* fbuf;
   KConst<double> cd;
   KConst<float> cf;
 };
@@ -106,6 +111,6 @@ void fill_kconst(const KParams& kp, KConst<T>& c) {
   c.cvTw2 = T(2.0 * kp.cv * kp.Tw);
 }
 
-constexpr int GEO_AFFINE = 0, GEO_STORED = 1;
+constexpr int GEO_AFFINE = 0, GEO_STORED = 1, GEO_FLY = 2;
 
 }  // namespace dgcns

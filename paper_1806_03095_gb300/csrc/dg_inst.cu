@@ -1,11 +1,13 @@
-// One (N, QC, QV) instantiation of the libdgcns kernels; compiled once per
-// entry of DGCNS_CONFIGS with -DINST_N=.. -DINST_QC=.. -DINST_QV=.. so that the
-// configurations build in parallel.
+// One part of one (N, QC, QV) instantiation of the libdgcns kernels; compiled once per entry of
+// DGCNS_CONFIGS and part 0..DGCNS_PARTS-1 with -DINST_N=.. -DINST_QC=.. -DINST_QV=.. -DINST_PART=..
+// so that everything builds in parallel.
 #include "dg_launch.cuh"
 
-#define DGCNS_CAT3(a, b, c) launchers_##a##_##b##_##c
-#define DGCNS_NAME(a, b, c) DGCNS_CAT3(a, b, c)
+#define DGCNS_CAT4(a, b, c, d) launchers_##a##_##b##_##c##_##d
+#define DGCNS_NAME(a, b, c, d) DGCNS_CAT4(a, b, c, d)
 
 namespace dgcns {
-Launchers DGCNS_NAME(INST_N, INST_QC, INST_QV)() { return make_launchers<INST_N, INST_QC, INST_QV>(); }
+void DGCNS_NAME(INST_N, INST_QC, INST_QV, INST_PART)(Launchers& L) {
+  fill_launchers<INST_N, INST_QC, INST_QV, INST_PART>(L);
+}
 }  // namespace dgcns

@@ -311,6 +311,172 @@ __device__ __forceinline__ int face_node(int d, int id, int j1, int j2) {
 }
 
 // ---------------------------------------------------------------------------
+// Geometry of the isoparametric map from the degree-k node coordinates X
+// ([CB][3][N^3]): interpolation to a point set and collocation derivatives
+// (exact, x is of degree k) give J[a][b] = d x_a / d xi_b; each point stores
+// J^{-1}[b][a] (index 3b+a) and |det J|, faces also the unit outward normal
+// n = J^{-T} n_xi / |J^{-T} n_xi| and dA = |det J| |J^{-T} n_xi|
+// (Eq. IntegralsReferenceSpace).  Used once in FP64 by the geometry kernel
+// (stored geometry) and per phase inside the operator kernels (GEO_FLY).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T inv3(const T J[3][3], T Ji[9]) {
+  const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const T id = T(1) / det;
+  Ji[0] = c00 * id;
+  Ji[1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[3] = c01 * id;
+  Ji[4] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[5] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[6] = c02 * id;
+  Ji[7] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[8] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+template <int N, int Q>
+constexpr int fill_cell_tmp() { return 3 * (N * N * Q + N * Q * Q + 4 * Q * Q * Q); }
+template <int N, int Q>
+constexpr int fill_face_tmp() { return 6 * N * N + 3 * N * Q + 12 * Q * Q; }
+
+// out[e][10][Q^3]: J^{-1} and |det J| at the Gauss points (Q per direction), matrices eS: N->Q, eD: Q->Q
+template <typename T, int N, int Q, int CB, class G>
+__device__ void fill_cell_geo(const T* X, T* buf, const T* eS, const T* eD, T* out, int nb, G grp) {
+  constexpr int P = Q * Q * Q;
+  T* A = buf;
+  T* B = A + CB * 3 * N * N * Q;
+  T* Xq = B + CB * 3 * N * Q * Q;
+  T* J0 = Xq + CB * 3 * P;
+  T* J1 = J0 + CB * 3 * P;
+  T* J2 = J1 + CB * 3 * P;
+  const int nbl = 3 * nb;
+  sweep<T, 0, N, N, N, Q, 1, false>(X, A, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 1, Q, N, N, Q, 1, false>(A, B, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 2, Q, Q, N, Q, 1, false>(B, Xq, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 0, Q, Q, Q, Q, -1, false>(Xq, J0, eD, nbl, grp);
+  sweep<T, 1, Q, Q, Q, Q, -1, false>(Xq, J1, eD, nbl, grp);
+  sweep<T, 2, Q, Q, Q, Q, -1, false>(Xq, J2, eD, nbl, grp);
+  grp.sync();
+  for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
+    const int e = idx / P, p = idx - e * P;
+    T J[3][3], Ji[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      J[a][0] = J0[(e * 3 + a) * P + p];
+      J[a][1] = J1[(e * 3 + a) * P + p];
+      J[a][2] = J2[(e * 3 + a) * P + p];
+    }
+    const T det = fabs(inv3(J, Ji));
+    T* o = out + (size_t)e * 10 * P + p;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) o[m * P] = Ji[m];
+    o[9 * P] = det;
+  }
+  grp.sync();
+}
+
+// out[e][13][Q^2] on face (d, s): J^{-1} (9), unit outward normal (3), dA (1); dl = l_i' at the face
+template <typename T, int N, int Q, int CB, int d, class G>
+__device__ void fill_face_geo(const T* X, int s, T* buf, const T* eS, const T* eD, const T* dl, T* out, int nb,
+                              G grp) {
+  constexpr int P = Q * Q, N2 = N * N, N3 = N * N * N;
+  constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  T* L = buf;
+  T* Dn = L + CB * 3 * N2;
+  T* Tm = Dn + CB * 3 * N2;
+  T* Xf = Tm + CB * 3 * N * Q;
+  T* Jt1 = Xf + CB * 3 * P;
+  T* Jt2 = Jt1 + CB * 3 * P;
+  T* Jd = Jt2 + CB * 3 * P;
+  const int id = s ? N - 1 : 0;
+  const int nbl = 3 * nb;
+  for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
+    const int ea = idx / N2, j = idx - ea * N2;
+    const T* x = X + (size_t)ea * N3;
+    L[idx] = x[face_node<N>(d, id, j % N, j / N)];
+    T dn = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) dn += dl[i] * x[face_node<N>(d, i, j % N, j / N)];
+    Dn[idx] = dn;
+  }
+  grp.sync();
+  sweep<T, 0, N, N, 1, Q, 1, false>(L, Tm, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 1, Q, N, 1, Q, 1, false>(Tm, Xf, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 0, N, N, 1, Q, 1, false>(Dn, Tm, eS, nbl, grp);
+  grp.sync();
+  sweep<T, 1, Q, N, 1, Q, 1, false>(Tm, Jd, eS, nbl, grp);
+  sweep<T, 0, Q, Q, 1, Q, -1, false>(Xf, Jt1, eD, nbl, grp);
+  sweep<T, 1, Q, Q, 1, Q, -1, false>(Xf, Jt2, eD, nbl, grp);
+  grp.sync();
+  const T sgn = s ? T(1) : T(-1);
+  for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
+    const int e = idx / P, p = idx - e * P;
+    T J[3][3], Ji[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      J[a][t1] = Jt1[(e * 3 + a) * P + p];
+      J[a][t2] = Jt2[(e * 3 + a) * P + p];
+      J[a][d] = Jd[(e * 3 + a) * P + p];
+    }
+    const T det = fabs(inv3(J, Ji));
+    const T v0 = sgn * Ji[3 * d], v1 = sgn * Ji[3 * d + 1], v2 = sgn * Ji[3 * d + 2];
+    const T nv = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    T* o = out + (size_t)e * 13 * P + p;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) o[m * P] = Ji[m];
+    o[9 * P] = v0 / nv;
+    o[10 * P] = v1 / nv;
+    o[11 * P] = v2 / nv;
+    o[12 * P] = det * nv;
+  }
+  grp.sync();
+}
+
+// out[e][N^3]: |det J| at the k+1 mass points (interpolation eSm, collocation eDm)
+template <typename T, int N, int CB, class G>
+__device__ void fill_mass_geo(const T* X, T* buf, const T* eSm, const T* eDm, T* out, int nb, G grp) {
+  constexpr int N3 = N * N * N;
+  T* A = buf;
+  T* B = A + CB * 3 * N3;
+  T* Xq = B + CB * 3 * N3;
+  T* J0 = Xq + CB * 3 * N3;
+  T* J1 = J0 + CB * 3 * N3;
+  T* J2 = J1 + CB * 3 * N3;
+  const int nbl = 3 * nb;
+  sweep<T, 0, N, N, N, N, 1, false>(X, A, eSm, nbl, grp);
+  grp.sync();
+  sweep<T, 1, N, N, N, N, 1, false>(A, B, eSm, nbl, grp);
+  grp.sync();
+  sweep<T, 2, N, N, N, N, 1, false>(B, Xq, eSm, nbl, grp);
+  grp.sync();
+  sweep<T, 0, N, N, N, N, -1, false>(Xq, J0, eDm, nbl, grp);
+  sweep<T, 1, N, N, N, N, -1, false>(Xq, J1, eDm, nbl, grp);
+  sweep<T, 2, N, N, N, N, -1, false>(Xq, J2, eDm, nbl, grp);
+  grp.sync();
+  for (int idx = grp.rank(); idx < nb * N3; idx += grp.size()) {
+    const int e = idx / N3, p = idx - e * N3;
+    T J[3][3], Ji[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      J[a][0] = J0[(e * 3 + a) * N3 + p];
+      J[a][1] = J1[(e * 3 + a) * N3 + p];
+      J[a][2] = J2[(e * 3 + a) * N3 + p];
+    }
+    out[(size_t)e * N3 + p] = fabs(inv3(J, Ji));
+  }
+  grp.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Shared-memory budget per kernel
 // ---------------------------------------------------------------------------
 template <int N, int QC, int QV>
@@ -324,6 +490,18 @@ struct Sizes {
   static constexpr int FACE_VISC = 4 * 5 * N2 + 5 * QV * N + 8 * 5 * QV * QV;
   static constexpr int FACE_ARENA = FACE_CONV > FACE_VISC ? FACE_CONV : FACE_VISC;
   static constexpr int MASS_ARENA = 2 * 5 * N3;
+  // GEO_FLY: fill temporaries live in the arena (computed before the phase uses it); the outputs in a
+  // separate per-cell region (cell points, own + neighbour face points, mass points)
+  static constexpr int QM = QC > QV ? QC : QV;
+  static constexpr int FLY_TMP_C = fill_cell_tmp<N, QC>() > fill_cell_tmp<N, QV>() ? fill_cell_tmp<N, QC>()
+                                                                                       : fill_cell_tmp<N, QV>();
+  static constexpr int FLY_TMP_F = fill_face_tmp<N, QM>();
+  static constexpr int FLY_TMP_M = 18 * N3;
+  static constexpr int FLY_TMP = FLY_TMP_C > FLY_TMP_F ? (FLY_TMP_C > FLY_TMP_M ? FLY_TMP_C : FLY_TMP_M)
+                                                       : (FLY_TMP_F > FLY_TMP_M ? FLY_TMP_F : FLY_TMP_M);
+  static constexpr int FLY_OUT_C = 10 * (QC3 > QV3 ? QC3 : QV3);
+  static constexpr int FLY_OUT_F = 2 * 13 * QM * QM;
+  static constexpr int FLY_OUT = FLY_OUT_C > FLY_OUT_F ? (FLY_OUT_C > N3 ? FLY_OUT_C : N3) : (FLY_OUT_F > N3 ? FLY_OUT_F : N3);
 };
 
 // ---------------------------------------------------------------------------
@@ -333,17 +511,20 @@ struct Sizes {
 // ---------------------------------------------------------------------------
 template <typename T, int N, int QC, int QV, int CB, int GEO, class G = CtaGroup>
 __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph,
-                           int e0, int nb, G grp = G()) {
+                           int e0, int nb, G grp = G(), const T* sx = nullptr, T* go = nullptr) {
   const KConst<T>& kc = kconst<T>(kp);
   const T detJ = kc.detJ;
   const T hinv[3] = {kc.hinv[0], kc.hinv[1], kc.hinv[2]};
   const int nbl = nb * 5;
   if (kp.conv) {
     constexpr int P = QC * QC * QC;
+    // stored geometry of the CTA's cells: global arrays, or recomputed now into `go` (GEO_FLY)
+    const T* gcell = GEO == GEO_FLY ? go : static_cast<const T*>(kp.gcc) + (size_t)e0 * 10 * P;
+    if (GEO == GEO_FLY) fill_cell_geo<T, N, QC, CB>(sx, ar, tb.eSc, tb.eDc, go, nb, grp);
     T* F0 = ar;
     T* F1 = ar + CB * 5 * P;
     T* F2 = ar + 2 * CB * 5 * P;
-    T* G = ar + 3 * CB * 5 * P;
+    T* Gt = ar + 3 * CB * 5 * P;
     // interpolate to the convective Gauss grid (Eq. SumFactorization)
     sweep<T, 0, N, N, N, QC, 1, false>(su, F1, tb.eSc, nbl, grp);
     grp.sync();
@@ -373,7 +554,7 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
         }
       } else {
         // contravariant flux Ft_b = -|J| w sum_a J^{-1}[b][a] F[.][a]
-        const T* g = static_cast<const T*>(kp.gcc) + (size_t)(e0 + e) * 10 * P + p;
+        const T* g = gcell + (size_t)e * 10 * P + p;
         T Ji[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) Ji[m] = g[m * P];
@@ -389,15 +570,15 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       }
     }
     grp.sync();
-    // G = sum_d D_d^T Ft_d  (test with grad V in the collocation basis)
-    sweep<T, 0, QC, QC, QC, QC, -1, false>(F0, G, tb.eDcT, nbl, grp);
+    // Gt = sum_d D_d^T Ft_d  (test with grad V in the collocation basis)
+    sweep<T, 0, QC, QC, QC, QC, -1, false>(F0, Gt, tb.eDcT, nbl, grp);
     grp.sync();
-    sweep<T, 1, QC, QC, QC, QC, -1, true>(F1, G, tb.eDcT, nbl, grp);
+    sweep<T, 1, QC, QC, QC, QC, -1, true>(F1, Gt, tb.eDcT, nbl, grp);
     grp.sync();
-    sweep<T, 2, QC, QC, QC, QC, -1, true>(F2, G, tb.eDcT, nbl, grp);
+    sweep<T, 2, QC, QC, QC, QC, -1, true>(F2, Gt, tb.eDcT, nbl, grp);
     grp.sync();
     // back to the nodes: S^T along z, y, x
-    sweep<T, 2, QC, QC, QC, N, 1, false>(G, F0, tb.eScT, nbl, grp);
+    sweep<T, 2, QC, QC, QC, N, 1, false>(Gt, F0, tb.eScT, nbl, grp);
     grp.sync();
     sweep<T, 1, QC, QC, N, N, 1, false>(F0, F1, tb.eScT, nbl, grp);
     grp.sync();
@@ -406,6 +587,8 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
   }
   if (kp.visc) {
     constexpr int P = QV * QV * QV;
+    const T* gcell = GEO == GEO_FLY ? go : static_cast<const T*>(kp.gcv) + (size_t)e0 * 10 * P;
+    if (GEO == GEO_FLY) fill_cell_geo<T, N, QV, CB>(sx, ar, tb.eSv, tb.eDv, go, nb, grp);
     T* V0 = ar;
     T* V1 = ar + CB * 5 * P;
     T* V2 = ar + 2 * CB * 5 * P;
@@ -425,16 +608,16 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
       const int e = idx / P, p = idx - e * P;
       const int q0 = p % QV, q1 = (p / QV) % QV, q2 = p / (QV * QV);
       const T w = tb.wv[q0] * tb.wv[q1] * tb.wv[q2] * detJ;
-      T u[5], G[5][3], F[5][3];
+      T u[5], Gr[5][3], F[5][3];
       T* Vd[3] = {V1, V2, V3};
       if (GEO == GEO_AFFINE) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           u[c] = V0[(e * 5 + c) * P + p];
 #pragma unroll
-          for (int j = 0; j < 3; ++j) G[c][j] = Vd[j][(e * 5 + c) * P + p] * hinv[j];
+          for (int j = 0; j < 3; ++j) Gr[c][j] = Vd[j][(e * 5 + c) * P + p] * hinv[j];
         }
-        visc_flux(u, G, ph, F);
+        visc_flux(u, Gr, ph, F);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           const T s = w * hinv[j];
@@ -442,7 +625,7 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
           for (int c = 0; c < 5; ++c) Vd[j][(e * 5 + c) * P + p] = s * F[c][j];
         }
       } else {
-        const T* g = static_cast<const T*>(kp.gcv) + (size_t)(e0 + e) * 10 * P + p;
+        const T* g = gcell + (size_t)e * 10 * P + p;
         T Ji[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) Ji[m] = g[m * P];
@@ -452,9 +635,9 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
           u[c] = V0[(e * 5 + c) * P + p];
           const T g0 = Vd[0][(e * 5 + c) * P + p], g1 = Vd[1][(e * 5 + c) * P + p], g2 = Vd[2][(e * 5 + c) * P + p];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) G[c][a] = Ji[a] * g0 + Ji[3 + a] * g1 + Ji[6 + a] * g2;
+          for (int a = 0; a < 3; ++a) Gr[c][a] = Ji[a] * g0 + Ji[3 + a] * g1 + Ji[6 + a] * g2;
         }
-        visc_flux(u, G, ph, F);
+        visc_flux(u, Gr, ph, F);
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
@@ -490,7 +673,7 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
 template <typename T, int N, int QC, int QV, int CB, int d, int GEO, class G = CtaGroup>
 __device__ void face_terms(const T* su, const T* sn, const int* wall, const int* nbi, const T* tau_f, T* sr, T* fa,
                            const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int e0, int nb, int s,
-                           G grp = G()) {
+                           G grp = G(), const T* sx = nullptr, const T* sxn = nullptr, T* go = nullptr) {
   const int f = 2 * d + s, fo = 2 * d + (1 - s);  // own face, neighbour's face
   constexpr int N2 = N * N, N3 = N * N * N;
   constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
@@ -505,6 +688,10 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
 
   if (kp.conv) {
     constexpr int P = QC * QC;
+    // own face geometry: stored [Nc][6][13][P], or recomputed now into go [CB][13][P] (GEO_FLY)
+    const T* gfo = GEO == GEO_FLY ? go : static_cast<const T*>(kp.gfc) + ((size_t)e0 * 6 + f) * 13 * P;
+    const size_t gfs = GEO == GEO_FLY ? (size_t)13 * P : (size_t)6 * 13 * P;
+    if (GEO == GEO_FLY) fill_face_geo<T, N, QC, CB, d>(sx, s, fa, tb.eSc, tb.eDc, s ? tb.dl1 : tb.dl0, go, nb, grp);
     T* Lm = fa;                   // own face layer      [CB][5][N2]
     T* Lp = Lm + CB * 5 * N2;     // neighbour face layer
     T* Tm = Lp + CB * 5 * N2;     // tmp [CB][5][N][QC]
@@ -547,7 +734,7 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         for (int c = 0; c < 5; ++c)
           Um[(e * 5 + c) * P + p] = w * (T(0.5) * sgn * (fm[c] + fp[c]) + T(0.5) * lam * (um[c] - up[c]));
       } else {
-        const T* g = static_cast<const T*>(kp.gfc) + ((size_t)(e0 + e) * 6 + f) * 13 * P + p;
+        const T* g = gfo + e * gfs + p;
         const T n0 = g[9 * P], n1 = g[10 * P], n2 = g[11 * P];
         const T dw = g[12 * P] * tb.wc[p % QC] * tb.wc[p / QC];
         T fn[5];
@@ -580,6 +767,13 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
 
   if (kp.visc) {
     constexpr int P = QV * QV;
+    const T* gfo = GEO == GEO_FLY ? go : static_cast<const T*>(kp.gfv) + ((size_t)e0 * 6 + f) * 13 * P;
+    const size_t gfs = GEO == GEO_FLY ? (size_t)13 * P : (size_t)6 * 13 * P;
+    T* gnb = go + CB * 13 * P;  // GEO_FLY: the neighbours' face geometry
+    if (GEO == GEO_FLY) {
+      fill_face_geo<T, N, QV, CB, d>(sx, s, fa, tb.eSv, tb.eDv, s ? tb.dl1 : tb.dl0, go, nb, grp);
+      fill_face_geo<T, N, QV, CB, d>(sxn, 1 - s, fa, tb.eSv, tb.eDv, s ? tb.dl0 : tb.dl1, gnb, nb, grp);
+    }
     T* Lm = fa;                    // face layers and normal-derivative layers [CB][5][N2]
     T* Lp = Lm + CB * 5 * N2;
     T* Dm = Lp + CB * 5 * N2;
@@ -660,7 +854,7 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         }
       } else {
         // reference derivative directions: t1, t2, d  ->  physical G[c][a] = sum_b J^{-1}[b][a] g_b
-        const T* g = static_cast<const T*>(kp.gfv) + ((size_t)(e0 + e) * 6 + f) * 13 * P + p;
+        const T* g = gfo + e * gfs + p;
 #pragma unroll
         for (int m = 0; m < 9; ++m) Jm[m] = g[m * P];
         nrm[0] = g[9 * P];
@@ -669,7 +863,8 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         wgt = g[12 * P] * tb.wv[p % QV] * tb.wv[p / QV];
         T Jp[9];
         if (!wall[e]) {
-          const T* gp = static_cast<const T*>(kp.gfv) + ((size_t)nbi[e] * 6 + fo) * 13 * P + p;
+          const T* gp = GEO == GEO_FLY ? gnb + (size_t)e * 13 * P + p
+                                       : static_cast<const T*>(kp.gfv) + ((size_t)nbi[e] * 6 + fo) * 13 * P + p;
 #pragma unroll
           for (int m = 0; m < 9; ++m) Jp[m] = gp[m * P];
         } else {
@@ -772,7 +967,8 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
 // ---------------------------------------------------------------------------
 template <typename T, int N, int CB, int GEO, class G = CtaGroup>
 __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int e0, int nb,
-                             bool negate, bool add_force, G grp = G()) {
+                             bool negate, bool add_force, G grp = G(), const T* sx = nullptr, T* go = nullptr) {
+  if (GEO == GEO_FLY) fill_mass_geo<T, N, CB>(sx, ma, tb.eSm, tb.eDm, go, nb, grp);
   constexpr int N3 = N * N * N;
   const int nbl = nb * 5;
   T* A = ma;
@@ -792,7 +988,8 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
       w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] * detJ;
     else
       w = tb.wm[p % N] * tb.wm[(p / N) % N] * tb.wm[p / (N * N)] *
-          static_cast<const T*>(kp.gm)[(size_t)(e0 + idx / (5 * N3)) * N3 + p];
+          (GEO == GEO_FLY ? go[(size_t)(idx / (5 * N3)) * N3 + p]
+                          : static_cast<const T*>(kp.gm)[(size_t)(e0 + idx / (5 * N3)) * N3 + p]);
     A[idx] *= sg / w;
   }
   grp.sync();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "dg_adjoint.cuh"
+#include "dg_faces.cuh"
 #include "dg_kernels.cuh"
 #include "dg_launchers.h"
 
@@ -38,14 +39,30 @@ __global__ void dg_dev_kernel(const KParams kp, const double* __restrict__ U, T*
   }
 }
 
-template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS>
-constexpr size_t op_smem_bytes() {
+template <int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
+constexpr size_t op_arena_elems() {
   using S = Sizes<N, QC, QV>;
   size_t arena = 0;
   if (CELL) arena = (size_t)CB * S::CELL_ARENA;
   if (FACE && (size_t)CB * S::FACE_ARENA > arena) arena = (size_t)CB * S::FACE_ARENA;
   if (MASS && (size_t)CB * S::MASS_ARENA > arena) arena = (size_t)CB * S::MASS_ARENA;
-  const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * 5 * S::N3 * (FACE ? 3 : 2) + arena + 2 * CB;
+  if (GEO == GEO_FLY && (size_t)CB * S::FLY_TMP > arena) arena = (size_t)CB * S::FLY_TMP;
+  return (arena + 3) & ~(size_t)3;
+}
+
+// GEO_FLY: own and neighbour node coordinates [CB][3][N^3] and the per-phase geometry outputs
+template <int N, int QC, int QV, int CB, bool FACE, int GEO>
+constexpr size_t op_geo_elems() {
+  using S = Sizes<N, QC, QV>;
+  return GEO == GEO_FLY ? (size_t)CB * (3 * S::N3 * (FACE ? 2 : 1) + S::FLY_OUT) : 0;
+}
+
+template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
+constexpr size_t op_smem_bytes() {
+  using S = Sizes<N, QC, QV>;
+  const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * 5 * S::N3 * (FACE ? 3 : 2) +
+                       op_arena_elems<N, QC, QV, CB, CELL, FACE, MASS, GEO>() +
+                       op_geo_elems<N, QC, QV, CB, FACE, GEO>() + 2 * CB;
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
 }
 
@@ -72,11 +89,10 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
   T* sr = su + CB * 5 * N3;
   T* sn = sr + CB * 5 * N3;
   T* ar = sn + (FACE ? CB * 5 * N3 : 0);
-  size_t arena = 0;
-  if (CELL) arena = (size_t)CB * S::CELL_ARENA;
-  if (FACE && (size_t)CB * S::FACE_ARENA > arena) arena = (size_t)CB * S::FACE_ARENA;
-  if (MASS && (size_t)CB * S::MASS_ARENA > arena) arena = (size_t)CB * S::MASS_ARENA;
-  T* tau_f = ar + arena;
+  T* sx = ar + op_arena_elems<N, QC, QV, CB, CELL, FACE, MASS, GEO>();  // GEO_FLY only
+  T* sxn = sx + CB * 3 * N3;
+  T* go = sxn + (FACE ? CB * 3 * N3 : 0);
+  T* tau_f = sx + op_geo_elems<N, QC, QV, CB, FACE, GEO>();
   int* wall = reinterpret_cast<int*>(tau_f + CB);
   int* nbi = wall + CB;
 
@@ -94,9 +110,27 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
     if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
     sr[i] = CELL ? T(0) : Rin[base + i];
   }
+  if (GEO == GEO_FLY) {
+    const T* X = static_cast<const T*>(kp.xyzT) + (size_t)e0 * 3 * N3;
+    for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) sx[i] = X[i];
+  }
   __syncthreads();
 
-  if (CELL) cell_terms<T, N, QC, QV, CB, GEO>(su, sr, ar, tb, kp, ph, e0, nb);
+  if (CELL) cell_terms<T, N, QC, QV, CB, GEO>(su, sr, ar, tb, kp, ph, e0, nb, CtaGroup(), sx, go);
+
+  if (CELL && !FACE && kp.fbuf != nullptr) {
+    // face-centric organisation: add the face shares of the batch (contiguous), staged in the arena
+    const T* F = static_cast<const T*>(kp.fbuf) + (size_t)e0 * fbuf_per_cell<N>();
+    __syncthreads();
+    if constexpr (S::CELL_ARENA >= fbuf_per_cell<N>()) {
+      for (int i = threadIdx.x; i < nb * fbuf_per_cell<N>(); i += blockDim.x) ar[i] = F[i];
+      __syncthreads();
+      gather_face_shares<T, N>(sr, ar, tb, nb, CtaGroup());
+    } else {
+      gather_face_shares<T, N>(sr, F, tb, nb, CtaGroup());
+    }
+    __syncthreads();
+  }
 
   if (FACE) {
     for (int d = 0; d < 3; ++d) {
@@ -126,16 +160,27 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
             sn[i] = Ud ? Ud[src] : T(U[src] - ref_of(kp, (i / N3) % 5));
           }
         }
+        if (GEO == GEO_FLY) {
+          for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) {
+            const int e = i / (3 * N3);
+            sxn[i] = wall[e] ? sx[i] : static_cast<const T*>(kp.xyzT)[(size_t)nbi[e] * 3 * N3 + (i - e * 3 * N3)];
+          }
+        }
         __syncthreads();
-        if (d == 0) face_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
-        if (d == 1) face_terms<T, N, QC, QV, CB, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
-        if (d == 2) face_terms<T, N, QC, QV, CB, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s);
+        const CtaGroup cg;
+        if (d == 0)
+          face_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s, cg, sx, sxn, go);
+        if (d == 1)
+          face_terms<T, N, QC, QV, CB, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s, cg, sx, sxn, go);
+        if (d == 2)
+          face_terms<T, N, QC, QV, CB, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, nb, s, cg, sx, sxn, go);
       }
     }
   }
 
   if (MASS)
-    inverse_mass<T, N, CB, GEO>(su, sr, ar, tb, kp, e0, nb, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0);
+    inverse_mass<T, N, CB, GEO>(su, sr, ar, tb, kp, e0, nb, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0,
+                                CtaGroup(), sx, go);
 
   if (kp.out_mode == 2) {
     // 2N update: dU in the residual type, the state accumulated in FP64
@@ -521,6 +566,9 @@ __global__ void __launch_bounds__(NT) dg_geom_kernel(const KParams kp, const dou
 template <int N, int QC, int QV>
 int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, double* gfc, double* gfv, double* gm,
                 double* tau, double* vol, double nu_kk, cudaStream_t st) {
+  if constexpr (!Feat<N, QC, QV>::geo) {
+    return -2;
+  } else {
   auto k = dg_geom_kernel<N, QC, QV>;
   constexpr size_t smem = (table_elems<N, QC, QV>() + 3 * N * N * N + geom_buf_elems<N, QC, QV>() + 8) * sizeof(double);
   if (smem > 227 * 1024) return -2;
@@ -531,6 +579,7 @@ int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, 
   }
   k<<<kp.Nc, NT, smem, st>>>(kp, xyz, gcc, gcv, gfc, gfv, gm, tau, vol, nu_kk);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -608,7 +657,8 @@ int ekgrad_launch_geo(const KParams& kp, const double* U, double* G, double inv_
 template <int N, int QC, int QV>
 int ekgrad_launch(const KParams& kp, const double* U, double* G, double inv_volume, cudaStream_t st) {
   if (kp.gcc == nullptr) return ekgrad_launch_geo<N, QC, QV, GEO_AFFINE>(kp, U, G, inv_volume, st);
-  return ekgrad_launch_geo<N, QC, QV, GEO_STORED>(kp, U, G, inv_volume, st);
+  if constexpr (Feat<N, QC, QV>::geo) return ekgrad_launch_geo<N, QC, QV, GEO_STORED>(kp, U, G, inv_volume, st);
+  return -2;
 }
 
 // ---------------------------------------------------------------------------
@@ -618,7 +668,8 @@ template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool 
 int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
               cudaStream_t st) {
   auto k = dg_op_kernel<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>;
-  constexpr size_t smem = op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS>();
+  constexpr size_t smem = op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
+  if (smem > 227 * 1024) return -2;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
@@ -637,21 +688,18 @@ int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, v
 // hide each other's latency.  Shared memory: the tables (per CTA) and one
 // private slice per warp.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, bool CELL, bool FACE, bool MASS>
+template <typename T, int N, int QC, int QV, bool CELL, bool FACE, bool MASS, int GEO>
 constexpr int warp_slice_elems() {
   using S = Sizes<N, QC, QV>;
-  int arena = 0;
-  if (CELL) arena = S::CELL_ARENA;
-  if (FACE && S::FACE_ARENA > arena) arena = S::FACE_ARENA;
-  if (MASS && S::MASS_ARENA > arena) arena = S::MASS_ARENA;
-  const int e = 5 * S::N3 * (FACE ? 3 : 2) + arena + 1 + 2 * 8 / (int)sizeof(T) + 2;
+  const int e = 5 * S::N3 * (FACE ? 3 : 2) + (int)op_arena_elems<N, QC, QV, 1, CELL, FACE, MASS, GEO>() +
+                (int)op_geo_elems<N, QC, QV, 1, FACE, GEO>() + 1 + 2 * 8 / (int)sizeof(T) + 2;
   return (e + 7) & ~7;
 }
 
-template <typename T, int N, int QC, int QV, int WPC, bool CELL, bool FACE, bool MASS>
+template <typename T, int N, int QC, int QV, int WPC, bool CELL, bool FACE, bool MASS, int GEO>
 constexpr size_t warp_smem_bytes() {
-  return ((size_t)table_elems<N, QC, QV>() + (size_t)WPC * warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS>()) *
-             sizeof(T) + 64;
+  return ((size_t)table_elems<N, QC, QV>() +
+          (size_t)WPC * warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS, GEO>()) * sizeof(T) + 64;
 }
 
 template <typename T, int N, int QC, int QV, int WPC, bool CELL, bool FACE, bool MASS, int GEO>
@@ -659,7 +707,7 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
                                                               const T* Rin, T* Rout, T* dU, double* Uout) {
   using S = Sizes<N, QC, QV>;
   constexpr int N3 = S::N3;
-  constexpr int SL = warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS>();
+  constexpr int SL = warp_slice_elems<T, N, QC, QV, CELL, FACE, MASS, GEO>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* stab = sm;
@@ -673,11 +721,10 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
   T* sr = su + 5 * N3;
   T* sn = sr + 5 * N3;
   T* ar = sn + (FACE ? 5 * N3 : 0);
-  int arena = 0;
-  if (CELL) arena = S::CELL_ARENA;
-  if (FACE && S::FACE_ARENA > arena) arena = S::FACE_ARENA;
-  if (MASS && S::MASS_ARENA > arena) arena = S::MASS_ARENA;
-  T* tau_f = ar + arena;
+  T* sx = ar + op_arena_elems<N, QC, QV, 1, CELL, FACE, MASS, GEO>();  // GEO_FLY only
+  T* sxn = sx + 3 * N3;
+  T* go = sxn + (FACE ? 3 * N3 : 0);
+  T* tau_f = sx + op_geo_elems<N, QC, QV, 1, FACE, GEO>();
   int* wall = reinterpret_cast<int*>(su + SL) - 2;  // two ints at the end of the slice
   int* nbi = wall + 1;
   const PhysT<T> ph = make_phys<T>(kp);
@@ -689,8 +736,24 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
     if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
     sr[i] = CELL ? T(0) : Rin[base + i];
   }
+  if (GEO == GEO_FLY) {
+    const T* X = static_cast<const T*>(kp.xyzT) + (size_t)e0 * 3 * N3;
+    for (int i = grp.rank(); i < 3 * N3; i += 32) sx[i] = X[i];
+  }
   grp.sync();
-  if (CELL) cell_terms<T, N, QC, QV, 1, GEO>(su, sr, ar, tb, kp, ph, e0, 1, grp);
+  if (CELL) cell_terms<T, N, QC, QV, 1, GEO>(su, sr, ar, tb, kp, ph, e0, 1, grp, sx, go);
+  if (CELL && !FACE && kp.fbuf != nullptr) {
+    const T* F = static_cast<const T*>(kp.fbuf) + (size_t)e0 * fbuf_per_cell<N>();
+    grp.sync();
+    if constexpr (S::CELL_ARENA >= fbuf_per_cell<N>()) {
+      for (int i = grp.rank(); i < fbuf_per_cell<N>(); i += 32) ar[i] = F[i];
+      grp.sync();
+      gather_face_shares<T, N>(sr, ar, tb, 1, grp);
+    } else {
+      gather_face_shares<T, N>(sr, F, tb, 1, grp);
+    }
+    grp.sync();
+  }
   if (FACE) {
     for (int d = 0; d < 3; ++d) {
       for (int s = 0; s < 2; ++s) {
@@ -715,16 +778,26 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
           const size_t nb0 = (size_t)nbi[0] * 5 * N3;
           for (int i = grp.rank(); i < nvals; i += 32)
             sn[i] = Ud ? Ud[nb0 + i] : T(U[nb0 + i] - ref_of(kp, (i / N3) % 5));
+          if (GEO == GEO_FLY) {
+            const T* Xn = static_cast<const T*>(kp.xyzT) + (size_t)nbi[0] * 3 * N3;
+            for (int i = grp.rank(); i < 3 * N3; i += 32) sxn[i] = Xn[i];
+          }
+        } else if (GEO == GEO_FLY) {
+          for (int i = grp.rank(); i < 3 * N3; i += 32) sxn[i] = sx[i];
         }
         grp.sync();
-        if (d == 0) face_terms<T, N, QC, QV, 1, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
-        if (d == 1) face_terms<T, N, QC, QV, 1, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
-        if (d == 2) face_terms<T, N, QC, QV, 1, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp);
+        if (d == 0)
+          face_terms<T, N, QC, QV, 1, 0, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp, sx, sxn, go);
+        if (d == 1)
+          face_terms<T, N, QC, QV, 1, 1, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp, sx, sxn, go);
+        if (d == 2)
+          face_terms<T, N, QC, QV, 1, 2, GEO>(su, sn, wall, nbi, tau_f, sr, ar, tb, kp, ph, e0, 1, s, grp, sx, sxn, go);
       }
     }
   }
   if (MASS)
-    inverse_mass<T, N, 1, GEO>(su, sr, ar, tb, kp, e0, 1, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0, grp);
+    inverse_mass<T, N, 1, GEO>(su, sr, ar, tb, kp, e0, 1, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0, grp,
+                               sx, go);
   if (kp.out_mode == 2) {
     const T A = T(kp.A), dt = T(kp.dt);
     const double B = kp.B;
@@ -742,7 +815,7 @@ template <typename T, int N, int QC, int QV, bool CELL, bool FACE, bool MASS, in
 int launch_op_warp(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
                    cudaStream_t st) {
   constexpr int WPC = 4;
-  constexpr size_t smem = warp_smem_bytes<T, N, QC, QV, WPC, CELL, FACE, MASS>();
+  constexpr size_t smem = warp_smem_bytes<T, N, QC, QV, WPC, CELL, FACE, MASS, GEO>();
   if (smem > 227 * 1024) return -2;
   auto k = dg_op_warp_kernel<T, N, QC, QV, WPC, CELL, FACE, MASS, GEO>;
   static bool attr = false;
@@ -756,28 +829,34 @@ int launch_op_warp(const KParams& kp, const double* U, const void* Rin, void* Ro
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <typename T, int N, int QC, int QV, int GEO, bool WARP, bool CELL, bool FACE, bool MASS>
+int launch_op_any(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
+                  cudaStream_t st) {
+  if constexpr (WARP) {
+    return launch_op_warp<T, N, QC, QV, CELL, FACE, MASS, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+  } else {
+    constexpr int CB = cells_per_cta<T, N, QC, QV>();
+    return launch_op<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+  }
+}
+
 template <typename T, int N, int QC, int QV, int GEO>
 int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU,
                     double* Uout, cudaStream_t st) {
-  constexpr int CB = cells_per_cta<T, N, QC, QV>();
   // FP32: warp per cell (latency-bound otherwise); FP64: CTA per cell batch (FP64-pipe bound)
-  constexpr bool WARP = sizeof(T) == 4 && warp_smem_bytes<T, N, QC, QV, 4, true, true, true>() <= 227 * 1024;
+  constexpr bool WARP = sizeof(T) == 4 && warp_smem_bytes<T, N, QC, QV, 4, true, true, true, GEO>() <= 227 * 1024;
   switch (mode) {
-    case OP_CELL:
-      return WARP ? launch_op_warp<T, N, QC, QV, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
-                  : launch_op<T, N, QC, QV, CB, true, false, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_FACE:
-      return WARP ? launch_op_warp<T, N, QC, QV, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
-                  : launch_op<T, N, QC, QV, CB, false, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_MASS:
-      return WARP ? launch_op_warp<T, N, QC, QV, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st)
-                  : launch_op<T, N, QC, QV, CB, false, false, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_CELL: return launch_op_any<T, N, QC, QV, GEO, WARP, true, false, false>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_FACE: return launch_op_any<T, N, QC, QV, GEO, WARP, false, true, false>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_MASS: return launch_op_any<T, N, QC, QV, GEO, WARP, false, false, true>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_FACE:
-      return WARP ? launch_op_warp<T, N, QC, QV, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st)
-                  : launch_op<T, N, QC, QV, CB, true, true, false, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+      return launch_op_any<T, N, QC, QV, GEO, WARP, true, true, false>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_CELL | OP_MASS:
+      if constexpr (Feat<N, QC, QV>::faces)
+        return launch_op_any<T, N, QC, QV, GEO, WARP, true, false, true>(kp, U, Rin, Rout, dU, Uout, st);
+      return -2;
     case OP_CELL | OP_FACE | OP_MASS:
-      return WARP ? launch_op_warp<T, N, QC, QV, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st)
-                  : launch_op<T, N, QC, QV, CB, true, true, true, GEO>(kp, U, Rin, Rout, dU, Uout, st);
+      return launch_op_any<T, N, QC, QV, GEO, WARP, true, true, true>(kp, U, Rin, Rout, dU, Uout, st);
     default: return -2;
   }
 }
@@ -785,8 +864,20 @@ int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Ri
 template <typename T, int N, int QC, int QV>
 int op_dispatch(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
                 cudaStream_t st) {
-  if (kp.gcc == nullptr) return op_dispatch_geo<T, N, QC, QV, GEO_AFFINE>(mode, kp, U, Rin, Rout, dU, Uout, st);
-  return op_dispatch_geo<T, N, QC, QV, GEO_STORED>(mode, kp, U, Rin, Rout, dU, Uout, st);
+  using F = Feat<N, QC, QV>;
+  if constexpr (sizeof(T) == 4 && !F::fp32) {
+    return -2;
+  } else {
+    if (kp.xyzT != nullptr) {
+      if constexpr (F::fly) return op_dispatch_geo<T, N, QC, QV, GEO_FLY>(mode, kp, U, Rin, Rout, dU, Uout, st);
+      return -2;
+    }
+    if (kp.gcc != nullptr) {
+      if constexpr (F::geo) return op_dispatch_geo<T, N, QC, QV, GEO_STORED>(mode, kp, U, Rin, Rout, dU, Uout, st);
+      return -2;
+    }
+    return op_dispatch_geo<T, N, QC, QV, GEO_AFFINE>(mode, kp, U, Rin, Rout, dU, Uout, st);
+  }
 }
 
 template <typename TL, int N, int QC, int QV, int GEO>
@@ -811,8 +902,14 @@ int diag_launch_geo(const KParams& kp, const double* U, const void* LU, double* 
 template <typename TL, int N, int QC, int QV>
 int diag_launch(const KParams& kp, const double* U, const void* LU, double* partial, int* nblocks,
                 cudaStream_t st) {
-  if (kp.gcc == nullptr) return diag_launch_geo<TL, N, QC, QV, GEO_AFFINE>(kp, U, LU, partial, nblocks, st);
-  return diag_launch_geo<TL, N, QC, QV, GEO_STORED>(kp, U, LU, partial, nblocks, st);
+  using F = Feat<N, QC, QV>;
+  if constexpr (sizeof(TL) == 4 && !F::fp32) {
+    return -2;
+  } else {
+    if (kp.gcc == nullptr) return diag_launch_geo<TL, N, QC, QV, GEO_AFFINE>(kp, U, LU, partial, nblocks, st);
+    if constexpr (F::geo) return diag_launch_geo<TL, N, QC, QV, GEO_STORED>(kp, U, LU, partial, nblocks, st);
+    return -2;
+  }
 }
 
 template <typename T, int N>
@@ -822,23 +919,198 @@ int dev_launch(const KParams& kp, const double* U, void* D, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int N, int QC, int QV>
-Launchers make_launchers() {
-  Launchers L;
-  L.op_fp64 = op_dispatch<double, N, QC, QV>;
-  L.op_fp32 = op_dispatch<float, N, QC, QV>;
-  L.diag_fp64 = diag_launch<double, N, QC, QV>;
-  L.diag_fp32 = diag_launch<float, N, QC, QV>;
-  L.geom = geom_launch<N, QC, QV>;
-  L.adj_fp64 = adj_launch<double, N, QC, QV>;
-  L.adj_fp32 = adj_launch<float, N, QC, QV>;
-  L.prep_fp64 = adj_prep_launch<double>;
-  L.prep_fp32 = adj_prep_launch<float>;
-  L.ekgrad = ekgrad_launch<N, QC, QV>;
-  L.dev_fp32 = dev_launch<float, N>;
-  L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
-  L.cb_fp32 = cells_per_cta<float, N, QC, QV>();
-  return L;
+// ---------------------------------------------------------------------------
+// Face-centric face kernel: blockIdx.y = direction d.  Blocks [0, ceil(Nc/CB)) take the faces
+// at the upper side (s = 1) of every cell (interior faces with both shares, upper walls with
+// one); on a non-periodic direction the following blocks take the lower wall faces (s = 0) of
+// the cells with c_d = 0.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int QC, int QV, int CB, int GEO>
+constexpr size_t face_arena_elems() {
+  using S = Sizes<N, QC, QV>;
+  size_t arena = (size_t)CB * PairSizes<N, QC, QV>::ARENA;
+  if (GEO == GEO_FLY && (size_t)CB * S::FLY_TMP > arena) arena = (size_t)CB * S::FLY_TMP;
+  return (arena + 3) & ~(size_t)3;
+}
+
+template <typename T, int N, int QC, int QV, int CB, int GEO>
+constexpr size_t face_smem_bytes() {
+  using S = Sizes<N, QC, QV>;
+  const size_t geo = GEO == GEO_FLY ? (size_t)CB * (2 * 3 * S::N3 + S::FLY_OUT) : 0;
+  const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * 5 * S::N3 * 2 + (size_t)CB * 5 * S::N2 +
+                       face_arena_elems<T, N, QC, QV, CB, GEO>() + geo + CB;
+  return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
+}
+
+// Faces per CTA: the largest batch (<= 8) below ~112 KB of shared memory.
+template <typename T, int N, int QC, int QV>
+constexpr int faces_per_cta() {
+  using S = Sizes<N, QC, QV>;
+  constexpr int per_face = (2 * 5 * S::N3 + 5 * S::N2 + PairSizes<N, QC, QV>::ARENA) * (int)sizeof(T) + 16;
+  constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_face;
+  return cb < 1 ? 1 : (cb > 8 ? 8 : cb);
+}
+
+template <typename T, int N, int QC, int QV, int CB, int GEO>
+__global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams kp, const double* __restrict__ U,
+                                                                  T* __restrict__ FB) {
+  using S = Sizes<N, QC, QV>;
+  constexpr int N3 = S::N3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stab = reinterpret_cast<T*>(smem_raw);
+  T* su = stab + table_elems<N, QC, QV>();
+  T* sn = su + CB * 5 * N3;
+  T* lc = sn + CB * 5 * N3;
+  T* fa = lc + CB * 5 * S::N2;
+  T* sx = fa + face_arena_elems<T, N, QC, QV, CB, GEO>();  // GEO_FLY only
+  T* sxn = sx + CB * 3 * N3;
+  T* go = sxn + CB * 3 * N3;
+  T* tau_f = sx + (GEO == GEO_FLY ? CB * (2 * 3 * N3 + S::FLY_OUT) : 0);
+  int* eo = reinterpret_cast<int*>(tau_f + CB);
+  int* en = eo + CB;
+
+  const int d = blockIdx.y;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const int nstd = (kp.Nc + CB - 1) / CB;
+  int s, i0, nitems;
+  if ((int)blockIdx.x < nstd) {
+    s = 1;
+    i0 = blockIdx.x * CB;
+    nitems = kp.Nc;
+  } else {
+    if (kp.periodic[d]) return;
+    s = 0;
+    i0 = (blockIdx.x - nstd) * CB;
+    nitems = kp.nc[t1] * kp.nc[t2];
+    if (i0 >= nitems) return;
+  }
+  const int nb = min(CB, nitems - i0);
+  const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
+  const PhysT<T> ph = make_phys<T>(kp);
+  if ((int)threadIdx.x < nb) {
+    const int i = i0 + threadIdx.x;
+    int c[3];
+    if (s == 1) {
+      c[0] = i % kp.nc[0];
+      c[1] = (i / kp.nc[0]) % kp.nc[1];
+      c[2] = i / (kp.nc[0] * kp.nc[1]);
+    } else {
+      c[d] = 0;
+      c[t1] = i % kp.nc[t1];
+      c[t2] = i / kp.nc[t1];
+    }
+    const int e = c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+    c[d] += s ? 1 : -1;
+    int w = 0;
+    if (c[d] < 0 || c[d] >= kp.nc[d]) {
+      if (kp.periodic[d])
+        c[d] = (c[d] + kp.nc[d]) % kp.nc[d];
+      else
+        w = 1;
+    }
+    const int n = w ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+    eo[threadIdx.x] = e;
+    en[threadIdx.x] = n;
+    const double te = kp.tau[e];
+    tau_f[threadIdx.x] = T(w ? te : fmax(te, kp.tau[n]));
+  }
+  __syncthreads();
+  const T* Ud = static_cast<const T*>(kp.Udev);
+  for (int i = threadIdx.x; i < nb * 5 * N3; i += blockDim.x) {
+    const int b = i / (5 * N3), r = i - b * 5 * N3;
+    const size_t so = (size_t)eo[b] * 5 * N3 + r;
+    su[i] = Ud ? Ud[so] : T(U[so] - ref_of(kp, r / N3));
+    if (en[b] >= 0) {
+      const size_t sq = (size_t)en[b] * 5 * N3 + r;
+      sn[i] = Ud ? Ud[sq] : T(U[sq] - ref_of(kp, r / N3));
+    }
+  }
+  if (GEO == GEO_FLY) {
+    const T* X = static_cast<const T*>(kp.xyzT);
+    for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) {
+      const int b = i / (3 * N3), r = i - b * 3 * N3;
+      sx[i] = X[(size_t)eo[b] * 3 * N3 + r];
+      sxn[i] = X[(size_t)(en[b] >= 0 ? en[b] : eo[b]) * 3 * N3 + r];
+    }
+  }
+  __syncthreads();
+  const CtaGroup cg;
+  if (d == 0)
+    face_pair_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+  else if (d == 1)
+    face_pair_terms<T, N, QC, QV, CB, 1, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+  else
+    face_pair_terms<T, N, QC, QV, CB, 2, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+}
+
+template <typename T, int N, int QC, int QV, int GEO>
+int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) {
+  constexpr int CB = faces_per_cta<T, N, QC, QV>();
+  constexpr size_t smem = face_smem_bytes<T, N, QC, QV, CB, GEO>();
+  if (smem > 227 * 1024) return -2;
+  auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    attr = true;
+  }
+  int extra = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (kp.periodic[d]) continue;
+    const int plane = kp.nc[d == 0 ? 1 : 0] * kp.nc[d == 2 ? 1 : 2];
+    const int nbk = (plane + CB - 1) / CB;
+    if (nbk > extra) extra = nbk;
+  }
+  const dim3 grid((kp.Nc + CB - 1) / CB + extra, 3);
+  k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T, int N, int QC, int QV>
+int faces_dispatch(const KParams& kp, const double* U, void* FB, cudaStream_t st) {
+  using F = Feat<N, QC, QV>;
+  if constexpr (!F::faces || (sizeof(T) == 4 && !F::fp32)) {
+    return -2;
+  } else {
+    if (kp.xyzT != nullptr) {
+      if constexpr (F::fly) return launch_faces<T, N, QC, QV, GEO_FLY>(kp, U, FB, st);
+      return -2;
+    }
+    if (kp.gcc != nullptr) {
+      if constexpr (F::geo) return launch_faces<T, N, QC, QV, GEO_STORED>(kp, U, FB, st);
+      return -2;
+    }
+    return launch_faces<T, N, QC, QV, GEO_AFFINE>(kp, U, FB, st);
+  }
+}
+
+// One part of the launcher table of (N, QC, QV); each part is its own translation unit so that the
+// instantiations compile in parallel.
+template <int N, int QC, int QV, int PART>
+void fill_launchers(Launchers& L) {
+  if constexpr (PART == 0) {  // FP64 operator
+    L.features = Feat<N, QC, QV>::bits;
+    L.op_fp64 = op_dispatch<double, N, QC, QV>;
+    L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
+  } else if constexpr (PART == 1) {  // FP32 operator (mixed form)
+    L.op_fp32 = op_dispatch<float, N, QC, QV>;
+    L.dev_fp32 = dev_launch<float, N>;
+    L.cb_fp32 = cells_per_cta<float, N, QC, QV>();
+  } else if constexpr (PART == 2) {  // diagnostics, geometry, kinetic-energy gradient
+    L.diag_fp64 = diag_launch<double, N, QC, QV>;
+    L.diag_fp32 = diag_launch<float, N, QC, QV>;
+    L.geom = geom_launch<N, QC, QV>;
+    L.ekgrad = ekgrad_launch<N, QC, QV>;
+  } else if constexpr (PART == 3) {  // adjoint
+    L.adj_fp64 = adj_launch<double, N, QC, QV>;
+    L.adj_fp32 = adj_launch<float, N, QC, QV>;
+    L.prep_fp64 = adj_prep_launch<double>;
+    L.prep_fp32 = adj_prep_launch<float>;
+  } else if constexpr (PART == 4) {  // face-centric face kernel, FP64
+    L.faces_fp64 = faces_dispatch<double, N, QC, QV>;
+  } else {  // face-centric face kernel, FP32
+    L.faces_fp32 = faces_dispatch<float, N, QC, QV>;
+  }
 }
 
 }  // namespace dgcns

@@ -20,11 +20,32 @@ using GeomFn = int (*)(const KParams&, const double* xyz, double* gcc, double* g
 // Adjoint: G = -(dF/dU)^T Y (lamU == nullptr) or lamU += dt * that (out_mode 2 in kp).
 using AdjFn = int (*)(const KParams&, const double* U, const void* Y, void* G, double* lamU, cudaStream_t);
 using PrepFn = int (*)(size_t n, double A, double B, const double* lamU, void* lamdU, void* W, cudaStream_t);
+// Face-centric face integrals: the face shares of every cell into FB ([Nc][6][2][5][N^2]).
+using FaceFn = int (*)(const KParams&, const double* U, void* FB, cudaStream_t);
 // G = d e_k / dU (FP64), e_k = (1/V) int |u|^2 / 2 at the convective points.
 using EkGradFn = int (*)(const KParams&, const double* U, double* G, double inv_volume, cudaStream_t);
 
+// Feature bits of an instantiation (only what the workloads and tests use is compiled, to keep
+// the build short): FP32 (mixed form), stored non-affine geometry, geometry on the fly, adjoint,
+// the face-centric organisation.
+enum { FEAT_FP32 = 1, FEAT_GEO = 2, FEAT_FLY = 4, FEAT_ADJ = 8, FEAT_FACES = 16 };
+
+template <int N, int QC, int QV>
+struct Feat {
+  static constexpr bool rule = QC == (3 * (N - 1)) / 2 + 1 && QV == N;  // 3/2-rule convective, k+1 viscous
+  static constexpr bool fp32 = rule && (N == 4 || N == 5 || N == 6);   // k = 3, 4, 5
+  static constexpr bool geo = rule && (N == 3 || N == 4 || N == 6);    // k = 2, 3, 5
+  static constexpr bool fly = rule && N == 4;                          // k = 3
+  static constexpr bool adj = rule && (N == 3 || N == 4 || N == 5);    // k = 2, 3, 4
+  static constexpr bool faces = rule;
+  static constexpr int bits = (fp32 ? FEAT_FP32 : 0) | (geo ? FEAT_GEO : 0) | (fly ? FEAT_FLY : 0) |
+                              (adj ? FEAT_ADJ : 0) | (faces ? FEAT_FACES : 0);
+};
+
 struct Launchers {
+  int features;
   OpFn op_fp64, op_fp32;
+  FaceFn faces_fp64, faces_fp32;
   DiagFn diag_fp64, diag_fp32;
   GeomFn geom;
   AdjFn adj_fp64, adj_fp32;
@@ -48,7 +69,16 @@ struct Launchers {
   X(4, 5, 5)             \
   X(6, 6, 6)
 
-#define DGCNS_DECLARE(N, QC, QV) Launchers launchers_##N##_##QC##_##QV();
+// Parts of each instantiation (separate translation units): FP64 operator, FP32 operator,
+// diagnostics + geometry, adjoint, FP64 face kernel, FP32 face kernel.
+#define DGCNS_PARTS 6
+#define DGCNS_DECLARE(N, QC, QV)                     \
+  void launchers_##N##_##QC##_##QV##_0(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_1(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_2(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_3(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_4(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_5(Launchers&);
 DGCNS_CONFIGS(DGCNS_DECLARE)
 #undef DGCNS_DECLARE
 

@@ -230,10 +230,13 @@ std::vector<double> build_tables(int k, int QC, int QV) {
 
 struct Registry {
   int N, QC, QV;
-  Launchers (*make)();
+  void (*part[DGCNS_PARTS])(Launchers&);
 };
 
-#define DGCNS_ENTRY(N, QC, QV) {N, QC, QV, &launchers_##N##_##QC##_##QV},
+#define DGCNS_ENTRY(N, QC, QV)                                                                           \
+  {N, QC, QV,                                                                                            \
+   {&launchers_##N##_##QC##_##QV##_0, &launchers_##N##_##QC##_##QV##_1, &launchers_##N##_##QC##_##QV##_2, \
+    &launchers_##N##_##QC##_##QV##_3, &launchers_##N##_##QC##_##QV##_4, &launchers_##N##_##QC##_##QV##_5}},
 const Registry kRegistry[] = {DGCNS_CONFIGS(DGCNS_ENTRY)};
 #undef DGCNS_ENTRY
 
@@ -256,7 +259,9 @@ struct dgcns_ctx {
   double* d_tau = nullptr;
   void* d_R = nullptr;        // residual scratch (split kernels)
   float* d_dev = nullptr;     // FP32 deviation state U - U_ref (mixed form)
+  void* d_fb = nullptr;       // face shares [Nc][6][2][5][N^2] (face-centric organisation)
   double* g64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stored geometry, FP64 (gcc gcv gfc gfv gm)
+  void* d_xyz = nullptr;  // node coordinates in the residual precision (geometry on the fly)
   float* g32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the mixed form
   size_t gsize[5] = {0, 0, 0, 0, 0};
   double* d_partial = nullptr;
@@ -359,8 +364,10 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     return bad(DGCNS_ERR_INVALID_ARG, "physical parameters must be positive (gamma > 1)");
   if (prm->precision != DGCNS_FP64 && prm->precision != DGCNS_MIXED)
     return bad(DGCNS_ERR_INVALID_ARG, "precision must be DGCNS_FP64 or DGCNS_MIXED");
-  if (prm->kernel != DGCNS_KERNEL_SPLIT && prm->kernel != DGCNS_KERNEL_FUSED)
-    return bad(DGCNS_ERR_INVALID_ARG, "kernel must be DGCNS_KERNEL_SPLIT or DGCNS_KERNEL_FUSED");
+  if (prm->geometry != DGCNS_GEO_STORED && prm->geometry != DGCNS_GEO_ON_THE_FLY)
+    return bad(DGCNS_ERR_INVALID_ARG, "geometry must be DGCNS_GEO_STORED or DGCNS_GEO_ON_THE_FLY");
+  if (prm->kernel != DGCNS_KERNEL_SPLIT && prm->kernel != DGCNS_KERNEL_FUSED && prm->kernel != DGCNS_KERNEL_FACES)
+    return bad(DGCNS_ERR_INVALID_ARG, "kernel must be DGCNS_KERNEL_SPLIT, DGCNS_KERNEL_FUSED or DGCNS_KERNEL_FACES");
   if (mesh->mapping != DGCNS_MAP_AFFINE && mesh->mapping != DGCNS_MAP_CHANNEL && mesh->mapping != DGCNS_MAP_SINE)
     return bad(DGCNS_ERR_INVALID_ARG, "unknown mapping");
   if (mesh->mapping == DGCNS_MAP_CHANNEL && !(mesh->map_param > 0.0))
@@ -371,10 +378,19 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   bool found = false;
   for (const Registry& r : kRegistry)
     if (r.N == N && r.QC == prm->nq_conv && r.QV == prm->nq_visc) {
-      c->L = r.make();
+      c->L = Launchers{};
+      for (int q = 0; q < DGCNS_PARTS; ++q) r.part[q](c->L);
       found = true;
     }
   if (!found) return bad(DGCNS_ERR_UNSUPPORTED, "no instantiation for this (k, nq_conv, nq_visc)");
+  if (prm->precision == DGCNS_MIXED && !(c->L.features & FEAT_FP32))
+    return bad(DGCNS_ERR_UNSUPPORTED, "the mixed form is not compiled for this (k, nq_conv, nq_visc)");
+  if (prm->kernel == DGCNS_KERNEL_FACES && !(c->L.features & FEAT_FACES))
+    return bad(DGCNS_ERR_UNSUPPORTED, "the face-centric kernels are not compiled for this (k, nq_conv, nq_visc)");
+  if (mesh->mapping != DGCNS_MAP_AFFINE && !(c->L.features & FEAT_GEO))
+    return bad(DGCNS_ERR_UNSUPPORTED, "non-affine meshes are not compiled for this (k, nq_conv, nq_visc)");
+  if (mesh->mapping != DGCNS_MAP_AFFINE && prm->geometry == DGCNS_GEO_ON_THE_FLY && !(c->L.features & FEAT_FLY))
+    return bad(DGCNS_ERR_UNSUPPORTED, "geometry on the fly is not compiled for this (k, nq_conv, nq_visc)");
 
   c->Nc = (int)ncell;
   c->N = N;
@@ -421,8 +437,10 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice);
+  const size_t fb_bytes = (size_t)c->Nc * 60 * N * N * (prm->precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
   if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess ||
-      (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess)) {
+      (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess) ||
+      (prm->kernel == DGCNS_KERNEL_FACES && cudaMalloc(&c->d_fb, fb_bytes) != cudaSuccess)) {
     cudaGetLastError();
     dg_cns_destroy(c);
     return DGCNS_ERR_OOM;
@@ -487,7 +505,28 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
                              c->nu * (k + 1) * (k + 1), c->stream);
     c->launches += 1;
     const cudaError_t se = cudaStreamSynchronize(c->stream);
-    cudaFree(d_xyz);
+    if (prm->geometry == DGCNS_GEO_ON_THE_FLY) {
+      if (prm->precision == DGCNS_MIXED) {
+        float* x32 = nullptr;
+        if (cudaMalloc(&x32, xyz.size() * sizeof(float)) == cudaSuccess) {
+          d2f_kernel<<<1024, 256, 0, c->stream>>>(d_xyz, x32, xyz.size());
+          c->launches += 1;
+          cudaStreamSynchronize(c->stream);
+        }
+        cudaFree(d_xyz);
+        c->d_xyz = x32;
+      } else {
+        c->d_xyz = d_xyz;
+      }
+      if (!c->d_xyz) {
+        cudaGetLastError();
+        dg_cns_destroy(c);
+        g_create_err = "out of device memory (coordinates)";
+        return DGCNS_ERR_OOM;
+      }
+    } else {
+      cudaFree(d_xyz);
+    }
     if (rg == 0 && se == cudaSuccess) {
       std::vector<double> vol(c->Nc);
       cudaMemcpy(vol.data(), d_vol, vol.size() * sizeof(double), cudaMemcpyDeviceToHost);
@@ -526,6 +565,7 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
       kp.gm = c->g64[4];
     }
   }
+  kp.xyzT = c->d_xyz;  // the operator kernels recompute the Jacobians when set
   // diagnostics partial sums
   KParams kd = kp;
   kd.tables = c->d_tab64;
@@ -560,6 +600,8 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_tau);
   cudaFree(c->d_R);
   cudaFree(c->d_dev);
+  cudaFree(c->d_fb);
+  cudaFree(c->d_xyz);
   cudaFree(c->d_partial);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
@@ -599,7 +641,20 @@ static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const voi
   const OpFn f = c->prm.precision == DGCNS_MIXED ? c->L.op_fp32 : c->L.op_fp64;
   const int r = f(mode, kp, U, Rin, Rout, dU, Uout, c->stream);
   c->launches += 1;
+  if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "operator variant not compiled or too large for shared memory");
   if (r != 0) return cuda_fail(c, "operator kernel launch");
+  return DGCNS_OK;
+}
+
+// Face-centric organisation: every face once, the shares of both cells into d_fb; the cell kernel that
+// follows adds them (kp.fbuf).
+static int run_faces(dgcns_ctx* c, KParams& kp, const double* U) {
+  const FaceFn f = c->prm.precision == DGCNS_MIXED ? c->L.faces_fp32 : c->L.faces_fp64;
+  const int r = f(kp, U, c->d_fb, c->stream);
+  c->launches += 1;
+  if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "face kernel not compiled or too large for shared memory");
+  if (r != 0) return cuda_fail(c, "face kernel launch");
+  kp.fbuf = c->d_fb;
   return DGCNS_OK;
 }
 
@@ -618,6 +673,11 @@ static int eval_L(dgcns_ctx* c, KParams kp, const double* U, void* dst, void* dU
   const int rd = prep_dev(c, kp, U);
   if (rd) return rd;
   if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE | OP_MASS, kp, U, nullptr, dst, dU, Uout);
+  if (c->prm.kernel == DGCNS_KERNEL_FACES) {
+    const int rf = run_faces(c, kp, U);
+    if (rf) return rf;
+    return run_op(c, OP_CELL | OP_MASS, kp, U, nullptr, dst, dU, Uout);
+  }
   KParams k0 = kp;
   k0.out_mode = 0;
   int r = run_op(c, OP_CELL, k0, U, nullptr, c->d_R, nullptr, nullptr);
@@ -645,6 +705,11 @@ int dg_cns_apply(dgcns_ctx* c, const double* U, void* R, int op) {
       const int rd = prep_dev(c, kp, U);
       if (rd) return rd;
       if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE, kp, U, nullptr, R, nullptr, nullptr);
+      if (c->prm.kernel == DGCNS_KERNEL_FACES) {
+        const int rf = run_faces(c, kp, U);
+        if (rf) return rf;
+        return run_op(c, OP_CELL, kp, U, nullptr, R, nullptr, nullptr);
+      }
       int r = run_op(c, OP_CELL, kp, U, nullptr, R, nullptr, nullptr);
       if (r) return r;
       return run_op(c, OP_FACE, kp, U, R, R, nullptr, nullptr);
@@ -702,6 +767,7 @@ int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) 
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (!U || !W || !G) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
+  if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
   if (G == (const void*)U) return fail(c, DGCNS_ERR_INVALID_ARG, "G must not alias U");
   KParams km = c->kp;
   km.out_mode = 0;
@@ -724,6 +790,7 @@ int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_
   if (!U_in || !lam_U || !lam_dU) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
+  if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
   if ((const void*)lam_U == (const void*)U_in) return fail(c, DGCNS_ERR_INVALID_ARG, "lam_U must not alias U_in");
   const PrepFn prep = c->prm.precision == DGCNS_MIXED ? c->L.prep_fp32 : c->L.prep_fp64;
   // W = lam_dU + B lam_U (scratch), lam_dU <- A W

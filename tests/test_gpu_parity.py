@@ -71,7 +71,7 @@ CASES = [((2, 2, 2), 1), ((2, 2, 2), 2), ((2, 2, 2), 3), ((3, 2, 4), 3), ((2, 2,
          ((2, 2, 2), 6)]
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("ncells,k", CASES)
 def test_residual_fp64_random_state(ncells, k, kernel):
     g, op = pair(ncells, k, kernel=kernel)
@@ -82,9 +82,10 @@ def test_residual_fp64_random_state(ncells, k, kernel):
     assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
+@pytest.mark.parametrize("kernel", [0, 2])
 @pytest.mark.parametrize("what,op_code", [(WHAT_CONV, 2), (WHAT_VISC, 3)])
-def test_residual_terms_fp64(what, op_code):
-    g, op = pair((2, 3, 2), 3, kernel=0)
+def test_residual_terms_fp64(what, op_code, kernel):
+    g, op = pair((2, 3, 2), 3, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 7)
     out = g.apply(on_gpu(U), op=op_code)
     l2, mx = rel_err(out, op.residual(U, what))
@@ -100,15 +101,16 @@ def test_other_quadrature_rules(qc, qv):
     assert l2 < TOL64 and mx < TOL64
 
 
-def test_single_cell_periodic_box():
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_single_cell_periodic_box(kernel):
     """Degenerate mesh: one cell per direction, the cell is its own neighbour on every face."""
-    g, op = pair((1, 1, 1), 3)
+    g, op = pair((1, 1, 1), 3, kernel=kernel)
     U = inputs.random_state(1, 64, 9)
     l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
     assert l2 < TOL64 and mx < TOL64
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_walls_affine_box(kernel):
     """Non-periodic y axis: isothermal no-slip walls (mirror-state reading)."""
     g, op = pair((2, 3, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
@@ -119,8 +121,19 @@ def test_walls_affine_box(kernel):
     assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_walls_on_every_side_ragged_box(kernel):
+    """Walls on all six sides of a ragged 3x4x5 box: lower-wall faces in several batches per direction."""
+    g, op = pair((3, 4, 5), 2, periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1.5, 2.0, 2.5), Re=180.0, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 15)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
 # -- L(U), inverse mass, body force ------------------------------------------------------------------
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_L_fp64(kernel):
     g, op = pair((2, 2, 3), 3, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 10)
@@ -136,7 +149,7 @@ def test_inverse_mass_fp64(k):
     assert l2 < TOL64 and mx < TOL64
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_L_with_body_force_and_walls(kernel):
     g, op = pair((2, 2, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
                  body_force=(1.0, 0.0, 0.0), kernel=kernel)
@@ -146,7 +159,7 @@ def test_L_with_body_force_and_walls(kernel):
 
 
 # -- RK stages ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_rk_stage_fp64(kernel):
     g, op = pair((2, 2, 2), 3, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 12)
@@ -173,7 +186,19 @@ def test_rk_stage_split_in_place_allowed_fused_rejected():
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+def test_rk_stage_face_centric_in_place():
+    """The face-centric stage reads neighbours only in the face kernel, so U_out may alias U_in."""
+    g, op = pair((2, 3, 2), 3, kernel=2)
+    U0 = on_gpu(inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 16))
+    dU0 = on_gpu(inputs.uniform(U0.shape, 17))
+    Uo, dU1 = g.empty_state(), dU0.clone()
+    g.rk_stage(1, 1e-3, 0.0, U0, dU1, Uo)
+    Ui, dU2 = U0.clone(), dU0.clone()
+    g.rk_stage(1, 1e-3, 0.0, Ui, dU2, Ui)
+    assert torch.equal(Ui, Uo) and torch.equal(dU1, dU2)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_tgv_8cubed_ten_rk_steps_fp64(kernel):
     """Taylor--Green 8^3, k = 3, one operator evaluation plus 10 RK(5,4) steps at CFL 0.4."""
     g, op = pair((8, 8, 8), 3, kernel=kernel)
@@ -218,7 +243,7 @@ def test_diagnostics_nonfinite_reported():
 
 
 # -- mixed precision ----------------------------------------------------------------------------------
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_mixed_precision_error_bound(kernel):
     """FP32 cell/face arithmetic: residual error of a few FP32 ulps of the state scale."""
     g, op = pair((4, 4, 4), 3, precision=1, kernel=kernel)
@@ -242,10 +267,10 @@ def test_unsupported_configuration():
 
 # -- non-affine meshes: stored geometry (channel stretching, sinusoidal deformation) ----------------------
 def pair_mapped(ncells, k, mapping, param, periodic, lo, hi, precision=0, kernel=1, Re=1600.0, u_mach=0.0,
-                body_force=(0.0, 0.0, 0.0)):
+                body_force=(0.0, 0.0, 0.0), geometry=0):
     qc, qv = (3 * k) // 2 + 1, k + 1
     g = DGCNS(ncells, lo, hi, periodic, k, qc, qv, Re=Re, u_mach=u_mach, body_force=body_force, precision=precision,
-              kernel=kernel, mapping=mapping, map_param=param)
+              kernel=kernel, mapping=mapping, map_param=param, geometry=geometry)
     mesh = BoxMesh(ncells, lo, hi, periodic, k, mapping, param)
     phys = ph.Physics.from_numbers(Re, 0.71, 0.1, u_mach=(u_mach or None), body_force=body_force)
     return g, DGOperator(mesh, phys, qc, qv)
@@ -254,7 +279,7 @@ def pair_mapped(ncells, k, mapping, param, periodic, lo, hi, precision=0, kernel
 CHANNEL = dict(periodic=(1, 0, 1), lo=(0.0, -1.0, 0.0), hi=(2 * PI, 1.0, PI), Re=180.0, u_mach=18.3)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_channel_mesh_residual_and_L_fp64(kernel):
     g, op = pair_mapped((2, 3, 2), 3, 1, 1.8, kernel=kernel, body_force=(1.0, 0.0, 0.0), **CHANNEL)
     xyz = g.node_coords().cpu()
@@ -269,7 +294,7 @@ def test_channel_mesh_residual_and_L_fp64(kernel):
 
 
 @pytest.mark.parametrize("k", [2, 3, 5])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_deformed_periodic_mesh_fp64(k, kernel):
     g, op = pair_mapped((2, 2, 2), k, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 40 + k)
@@ -310,3 +335,51 @@ def test_channel_mixed_precision_error():
     U = inputs.channel_state(op.xyz, 1806)
     l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
     assert l2 < 1e-3 and mx < 1e-2, (l2, mx)
+
+
+# -- non-affine meshes: Jacobians recomputed in the operator kernels from the node coordinates -------------
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_channel_mesh_geometry_on_the_fly_fp64(kernel):
+    g, op = pair_mapped((2, 3, 2), 3, 1, 1.8, kernel=kernel, body_force=(1.0, 0.0, 0.0), geometry=1, **CHANNEL)
+    U = inputs.channel_state(op.xyz, 1807)
+    ref, t2, tm = fp64_tol(op.residual, U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), ref)
+    assert l2 < t2 and mx < tm, (l2, mx, t2, tm)
+    ref, t2, tm = fp64_tol(op.L, U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), ref)
+    assert l2 < t2 and mx < tm, (l2, mx, t2, tm)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_deformed_periodic_mesh_geometry_on_the_fly_fp64(kernel):
+    g, op = pair_mapped((3, 2, 2), 3, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, kernel=kernel, geometry=1)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 77)
+    for what in (WHAT_CONV, WHAT_VISC):
+        l2, mx = rel_err(g.apply(on_gpu(U), op=2 if what == WHAT_CONV else 3), op.residual(U, what))
+        assert l2 < TOL64 and mx < TOL64, (what, l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    dt = 1e-3
+    Ug = on_gpu(U)
+    g.rk_steps(1, dt, 0.0, Ug)
+    Ur = ork.step(lambda V, t: op.L(V), U, dt, 0.0)
+    l2, mx = rel_err(Ug - on_gpu(U), Ur - U)
+    assert l2 < 1e-9 and mx < 1e-9, (l2, mx)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_channel_geometry_on_the_fly_mixed_error(kernel):
+    g, op = pair_mapped((2, 4, 2), 3, 1, 1.8, precision=1, kernel=kernel, body_force=(1.0, 0.0, 0.0), geometry=1,
+                        **CHANNEL)
+    U = inputs.channel_state(op.xyz, 1806)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < 1e-3 and mx < 1e-2, (l2, mx)
+
+
+def test_geometry_on_the_fly_unsupported_and_invalid():
+    with pytest.raises(api.DGCNSError) as ei:
+        pair_mapped((2, 2, 2), 5, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, geometry=1)
+    assert ei.value.code == -2
+    with pytest.raises(api.DGCNSError) as ei:
+        pair_mapped((2, 2, 2), 3, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, geometry=7)
+    assert ei.value.code == -1
