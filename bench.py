@@ -2,7 +2,9 @@
 
 A step is one full RK(5,4) time step (5 stages, each one evaluation of
 L = M^{-1}(-F + F_rhs) with cell and face integrals, inverse mass and the 2N
-update) of the Taylor--Green vortex, 64^3 cells, k = 3, FP64, fused kernel.
+update) of the Taylor--Green vortex, 64^3 cells, k = 3, FP64, face-centric
+kernels (a face kernel that evaluates every face once, then one kernel for the
+cells, the face shares, M^{-1} and the update).
 Metric: GDoF/s per RK stage = 5 N_nodes * stages / time / 1e9 (DoF counts the
 5 conserved fields per node).
 
@@ -130,7 +132,10 @@ def run_stages(ctx, nsteps, dt, t0, bufs):
     return a
 
 
-def time_native(cfg, steps, warmup, device):
+def time_native(cfg, steps, warmup, device, kernel_times=None):
+    """Time `steps` RK(5,4) steps after `warmup` untimed ones (CUDA events on torch's current stream, where the
+    library launches).  kernel_times (dict): filled with the library's per-kernel CUDA-event times of the timed
+    region, {kind: (total ms, launches)}."""
     from paper_1806_03095_gb300 import configs, inputs
     ctx = configs.make_context(cfg, device=device)
     xyz = ctx.node_coords()
@@ -143,12 +148,17 @@ def time_native(cfg, steps, warmup, device):
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = ctx.dg_cns_launch_count()
+    if kernel_times is not None:
+        ctx.timing(True)
     e0.record(st)
     run_stages(ctx, steps, dt, 0.0, bufs)
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = ctx.dg_cns_launch_count() - n0
+    if kernel_times is not None:
+        kernel_times.update(ctx.kernel_times())
+        ctx.timing(False)
     return ctx, bufs, dt, ms, launches
 
 
@@ -163,7 +173,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="tgv64_k3")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--kernel", choices=["fused", "split", "faces"], default="fused")
+    ap.add_argument("--kernel", choices=["fused", "split", "faces"], default="faces")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -185,20 +195,14 @@ def main():
     barrier(ws)
     clocks = ClockSampler(device)
     clocks.start()
-    ctx, bufs, dt, ms, launches = time_native(cfg, args.steps, args.warmup, device)
+    ktimes = {}
+    ctx, bufs, dt, ms, launches = time_native(cfg, args.steps, args.warmup, device, ktimes)
     clk = clocks.stop()
     ms = allreduce_max(ws, ms)
     barrier(ws)
     stages = 5 * args.steps
     value = ws * 5 * nodes * stages / (ms * 1e-3) / 1e9
     ms_step = ms / args.steps
-    t_launch = ms * 1e-3 / stages if args.kernel == "fused" else None
-
-    peaks = load_peaks()
-    rbytes = 4 if prec else 8
-    flops = roofline.stage_flops_per_cell(N, cfg["nq_conv"], cfg["nq_visc"]) * Nc
-    bytes_launch = nodes * (roofline.stage_bytes_per_node(rbytes, True) + 4 * roofline.stage_bytes_per_node(rbytes))
-    bytes_launch /= 5.0
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 arithmetic / f64 state", "data": "synthetic",
@@ -209,18 +213,7 @@ def main():
                       "l2": "inputs larger than L2 (state %.0f MB per vector)" % (nodes * 40 / 1e6),
                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
            "gpu_launches": int(launches)}
-    if t_launch is not None:
-        peak = FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS
-        ach = flops / t_launch / 1e12
-        hbm = bytes_launch / t_launch / 1e9
-        hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        out["roofline"] = {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
-                           "frac": round(ach / peak, 4), "traffic": None,
-                           "peak_source": "measured %s FMA probe (no %s entry in MEASURED_PEAKS.json)"
-                           % ("FP32" if prec else "FP64", "FP32" if prec else "FP64"),
-                           "kernel": "dg_op_kernel (fused stage)", "flops_per_launch": flops,
-                           "hbm": {"achieved": round(hbm, 2), "peak": hbm_peak, "unit": "GB/s",
-                                   "frac": round(hbm / hbm_peak, 5), "bytes_per_launch": bytes_launch}}
+    out["roofline"] = roofline_entry(ktimes, cfg, prec, load_peaks())
     if clk:
         out["clocks"] = clk
 
@@ -235,6 +228,57 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+KERNEL_NAMES = {
+    "fused": "dg_op_kernel / dg_op_warp_kernel: cells + 6 faces + M^-1 + stage update (fused)",
+    "faces": "dg_face_kernel: every face once, both cells' shares (face-centric)",
+    "cell_stage": "dg_op_kernel / dg_op_warp_kernel: cells + face shares + M^-1 + stage update (face-centric)",
+    "cell": "dg_op_kernel: cell integrals (split)", "face": "dg_op_kernel: element-centric faces (split)",
+    "mass": "dg_op_kernel: M^-1 + stage update (split)", "dev": "dg_dev_kernel: FP32 deviation pre-pass"}
+
+
+def roofline_entry(ktimes, cfg, prec, peaks):
+    """ALU roofline of the dominant kernel (largest share of the timed region), from the library's per-kernel
+    CUDA-event times: achieved = algorithmic flops per launch / average launch duration; every kernel kind is
+    listed with its share, its flop rate and its algorithmic HBM rate."""
+    from paper_1806_03095_gb300 import roofline
+    N, QC, QV = cfg["k"] + 1, cfg["nq_conv"], cfg["nq_visc"]
+    Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
+    rbytes = 4 if prec else 8
+    peak = FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    total = sum(v[0] for v in ktimes.values()) or 1.0
+    kernels = {}
+    for kind, (kms, n) in ktimes.items():
+        t = kms / n * 1e-3
+        e = {"launches": n, "avg_ms": round(kms / n, 4), "share": round(kms / total, 4)}
+        fl = roofline.kernel_flops(kind, N, QC, QV, Nc)
+        by = roofline.kernel_bytes(kind, N, Nc, rbytes) if kind != "dev" else N ** 3 * Nc * 5 * (8 + rbytes)
+        if kind in ("fused", "cell_stage", "mass"):
+            by -= N ** 3 * Nc * 5 * rbytes / 5.0  # stage 0 of 5 does not read dU
+        if fl:
+            e["tflops"] = round(fl / t / 1e12, 4)
+            e["frac_alu"] = round(fl / t / 1e12 / peak, 4)
+        if by:
+            e["hbm_gbs"] = round(by / t / 1e9, 2)
+        kernels[kind] = e
+    if not ktimes:
+        return None
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    kms, n = ktimes[dom]
+    t = kms / n * 1e-3
+    fl = roofline.kernel_flops(dom, N, QC, QV, Nc) or 0.0
+    by = kernels[dom].get("hbm_gbs", 0.0) * 1e9 * t
+    ach = fl / t / 1e12
+    return {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+            "traffic": None,
+            "peak_source": "measured %s FMA probe (no %s entry in MEASURED_PEAKS.json)"
+            % ("FP32" if prec else "FP64", "FP32" if prec else "FP64"),
+            "kernel": KERNEL_NAMES.get(dom, dom), "avg_launch_ms": round(kms / n, 4), "flops_per_launch": fl,
+            "hbm": {"achieved": round(by / t / 1e9, 2), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(by / t / 1e9 / hbm_peak, 5), "bytes_per_launch": by},
+            "kernels": kernels}
 
 
 def e2e_native(ctx, bufs, dt, nsteps):
@@ -266,8 +310,9 @@ def extras(args, cfg):
     res = {}
     device = torch.cuda.current_device()
     steps = max(2, args.steps // 2)
-    for name, prec, kern in (("fp64_split", 0, 0), ("fp64_faces", 0, 2), ("mixed_fused", 1, 1), ("mixed_split", 1, 0),
-                             ("mixed_faces", 1, 2)):
+    combos = [("%s_%s" % ("fp64" if p == 0 else "mixed", kn), p, kv) for p in (0, 1)
+              for kn, kv in (("faces", 2), ("fused", 1), ("split", 0))]
+    for name, prec, kern in [c for c in combos if (c[1], c[2]) != (cfg["precision"], cfg["kernel"])]:
         c = dict(cfg, precision=prec, kernel=kern)
         ctx, bufs, dt, ms, _ = time_native(c, steps, 3, device)
         nodes = bufs[0].numel() // 5
@@ -275,8 +320,8 @@ def extras(args, cfg):
                      "ms_per_step": round(ms / steps, 3)}
         del ctx, bufs
         torch.cuda.empty_cache()
-    g64 = configs.make_context(dict(cfg, precision=0, kernel=1), device=device)
-    g32 = configs.make_context(dict(cfg, precision=1, kernel=1), device=device)
+    g64 = configs.make_context(dict(cfg, precision=0, kernel=2), device=device)
+    g32 = configs.make_context(dict(cfg, precision=1, kernel=2), device=device)
     U = inputs.tgv_state(g64.node_coords())
     L64 = g64.apply(U, op=api.OP_L)
     L32 = g32.apply(U, op=api.OP_L).double()
@@ -286,9 +331,12 @@ def extras(args, cfg):
                                   "rel_max": float(d.abs().max() / L64.abs().max())}
     del g64, g32, U, L64, L32, d
     torch.cuda.empty_cache()
-    res["adjoint"] = adjoint_cost()
+    res["adjoint"] = adjoint_cost(kernel=2)
+    res["adjoint_element_centric"] = adjoint_cost(kernel=1)
     res.update(other_workloads(steps))
     res["mixed_dissipation_history"] = dissipation_history()
+    res["memory_bound_kernels"] = memory_bound_kernels()
+    res["k_sweep"] = k_sweep()
     return res
 
 
@@ -307,7 +355,7 @@ def other_workloads(steps):
                                ("channel32_k3_mixed", "channel32_k3", 1, 0), ("channel32_k3_fp64", "channel32_k3", 0, 0),
                                ("channel32_k3_mixed_geometry_on_the_fly", "channel32_k3", 1, 1),
                                ("channel32_k3_fp64_geometry_on_the_fly", "channel32_k3", 0, 1)):
-        cfg = dict(configs.WORKLOADS[wl](precision=prec, kernel=1), geometry=geo)
+        cfg = dict(configs.WORKLOADS[wl](precision=prec, kernel=2), geometry=geo)
         ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
         nodes = bufs[0].numel() // 5
         out[key] = {"value": _rate(ms, nodes, steps), "unit": UNIT, "ms_per_step": round(ms / steps, 3), "dt": dt}
@@ -323,6 +371,75 @@ def other_workloads(steps):
                                            "rel_max": float(d.abs().max() / L64.abs().max())}
     del g64, g32, U, L64, d
     torch.cuda.empty_cache()
+    return out
+
+
+def memory_bound_kernels(reps=20):
+    """The kernels the HBM bar applies to: the inverse mass alone (dg_cns_inverse_mass: read R, write M^-1 R)
+    and the split organisation's M^-1 + stage-update kernel (read R, dU, U; write dU, U_out), TGV 64^3, k = 3,
+    FP64 and mixed, timed with the library's per-kernel CUDA events; both roofs reported (FP64 is ALU-bound
+    even here: ~3 flop/B of even-odd sweeps against a ridge of 0.18 flop/B)."""
+    from paper_1806_03095_gb300 import configs, inputs, roofline
+    device = torch.cuda.current_device()
+    hbm_peak = load_peaks().get("hbm_gbs", 6800.0)
+    out = {}
+    for prec in (0, 1):
+        cfg = configs.WORKLOADS["tgv64_k3"](precision=prec, kernel=0)
+        g = configs.make_context(cfg, device=device)
+        N = cfg["k"] + 1
+        Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
+        rb = 4 if prec else 8
+        R = inputs.uniform(g.shape, 5).to(device=device, dtype=g.rdtype)
+        Y = torch.empty_like(R)
+        for _ in range(3):
+            g.inverse_mass(R, Y)
+        g.timing(True)
+        for _ in range(reps):
+            g.inverse_mass(R, Y)
+        kt = g.kernel_times()
+        g.timing(False)
+        ms = kt["mass"][0] / kt["mass"][1]
+        by = 2 * Nc * N ** 3 * 5 * rb
+        fl = roofline.mass_flops(N) * Nc
+        peak = FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS
+        name = "fp64" if prec == 0 else "mixed"
+        out["inverse_mass_" + name] = {"avg_ms": round(ms, 4), "hbm_gbs": round(by / ms / 1e6, 1),
+                                       "hbm_frac": round(by / ms / 1e6 / hbm_peak, 4),
+                                       "tflops": round(fl / ms / 1e9, 3), "alu_frac": round(fl / ms / 1e9 / peak, 4),
+                                       "bytes_per_launch": by, "flops_per_launch": fl}
+        # split stage: the M^-1 + update kernel inside real RK steps
+        kt = {}
+        ctx, bufs, dt, ms_all, _ = time_native(cfg, 2, 3, device, kt)
+        mk = kt["mass"]
+        ms = mk[0] / mk[1]
+        fl = roofline.kernel_flops("mass", N, cfg["nq_conv"], cfg["nq_visc"], Nc)
+        by = roofline.kernel_bytes("mass", N, Nc, rb) - N ** 3 * Nc * 5 * rb / 5.0
+        out["split_mass_stage_" + name] = {"avg_ms": round(ms, 4), "hbm_gbs": round(by / ms / 1e6, 1),
+                                           "hbm_frac": round(by / ms / 1e6 / hbm_peak, 4),
+                                           "tflops": round(fl / ms / 1e9, 3),
+                                           "alu_frac": round(fl / ms / 1e9 / peak, 4), "bytes_per_launch": by}
+        del g, R, Y, ctx, bufs
+        torch.cuda.empty_cache()
+    return out
+
+
+def k_sweep(steps=2):
+    """Throughput against the polynomial degree (the paper's throughput-versus-k study, Sec. 3): TGV meshes of
+    about 84M DoFs for k = 2..6 (FP64) and k = 3..5 (mixed), fused and face-centric kernels."""
+    from paper_1806_03095_gb300 import configs
+    device = torch.cuda.current_device()
+    out = {}
+    for k in (2, 3, 4, 5, 6):
+        n = max(2, int(round((16.78e6 / (k + 1) ** 3) ** (1.0 / 3.0))))
+        for prec in ((0, 1) if k in (3, 4, 5) else (0,)):
+            for kern in (1, 2):
+                cfg = configs.tgv(n, k, precision=prec, kernel=kern)
+                ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+                nodes = bufs[0].numel() // 5
+                key = "k%d_%s_%s" % (k, "fp64" if prec == 0 else "mixed", "fused" if kern == 1 else "faces")
+                out[key] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps), "unit": UNIT}
+                del ctx, bufs
+                torch.cuda.empty_cache()
     return out
 
 
@@ -364,12 +481,13 @@ def dissipation_history(t_final=2.0, every=8):
             "final_fp64": float(a[-1]), "final_mixed": float(b[-1])}
 
 
-def adjoint_cost(nsteps=200, every=20):
+def adjoint_cost(nsteps=200, every=20, kernel=2):
     """Discrete adjoint of TGV 24^3, k = 4 (FP64): forward nsteps RK(5,4) steps with a checkpoint every `every`
     steps, then the gradient of the final kinetic energy with respect to the initial velocity field (recomputation
-    of the segments + stage adjoints).  Reports forward and gradient times and their ratio."""
+    of the segments + stage adjoints).  Reports forward and gradient times and their ratio.  kernel 2: face-centric
+    forward and adjoint kernels; kernel 1: element-centric (fused forward, element-centric adjoint kernel)."""
     from paper_1806_03095_gb300 import adjoint as adj, configs, inputs
-    cfg = configs.WORKLOADS["tgv24_k4"](precision=0, kernel=1)
+    cfg = configs.WORKLOADS["tgv24_k4"](precision=0, kernel=kernel)
     g = configs.make_context(cfg)
     U0 = inputs.tgv_state(g.node_coords())
     rho = U0[:, 0].clone()
@@ -388,9 +506,10 @@ def adjoint_cost(nsteps=200, every=20):
     torch.cuda.synchronize()
     fwd = ev[0].elapsed_time(ev[1])
     bwd = ev[1].elapsed_time(ev[2])
-    return {"workload": "TGV 24^3, k=4, FP64, %d RK(5,4) steps, checkpoint every %d" % (nsteps, every),
+    return {"workload": "TGV 24^3, k=4, FP64, %d RK(5,4) steps, checkpoint every %d, %s kernels"
+            % (nsteps, every, "face-centric" if kernel == 2 else "element-centric"),
             "forward_ms": round(fwd, 1), "gradient_ms": round(bwd, 1), "gradient_over_forward": round(bwd / fwd, 3),
-            "grad_norm": float(torch.linalg.norm(u0.grad)), "e_k_final": float(J)}
+            "grad_norm": float(torch.linalg.norm(u0.grad)), "e_k_final": float(J.detach())}
 
 
 # -- CPU oracle --------------------------------------------------------------------------------------

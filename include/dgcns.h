@@ -203,6 +203,30 @@ int dg_cns_diagnostics_noalloc(dgcns_ctx* ctx, const double* U, const void* L_of
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int dg_cns_launch_count(const dgcns_ctx* ctx, int64_t* count);
 
+/* Kernel kinds of the per-kernel timing. */
+#define DGCNS_KT_CELL 0        /* cell integrals alone (split organisation; residual of the face-centric one) */
+#define DGCNS_KT_FACE 1        /* element-centric face integrals alone (split organisation) */
+#define DGCNS_KT_MASS 2        /* inverse mass / stage update alone (split organisation, adjoint M^-1 W) */
+#define DGCNS_KT_FUSED 3       /* fused cells + 6 faces (+ M^-1 + stage update) */
+#define DGCNS_KT_FACES 4       /* face-centric face kernel (every face once) */
+#define DGCNS_KT_CELL_STAGE 5  /* cells + face shares + M^-1 + stage update (face-centric organisation) */
+#define DGCNS_KT_DEV 6         /* FP32 deviation pre-pass of the mixed form */
+#define DGCNS_KT_ADJ_PREP 7    /* adjoint stage preparation (W = lam_dU + B lam_U, lam_dU = A W) */
+#define DGCNS_KT_ADJ_FACES 8   /* face-centric adjoint face kernel */
+#define DGCNS_KT_ADJ 9         /* adjoint cell (+ element-centric face) kernel */
+#define DGCNS_KT_OTHER 10      /* diagnostics, kinetic-energy gradient */
+#define DGCNS_KT_COUNT 11
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around every kernel the
+   context launches.  enable != 0 clears the totals and starts timing; enable == 0 stops it (the
+   totals are kept).  Off by default. */
+int dg_cns_timing(dgcns_ctx* ctx, int enable);
+
+/* Synchronizes the context's stream, then writes for kinds 0..n-1 (n <= DGCNS_KT_COUNT) the total
+   device time ms[i] (milliseconds) and the number of timed launches counts[i] since timing was
+   enabled.  Either pointer may be NULL. */
+int dg_cns_kernel_times(dgcns_ctx* ctx, double* ms, int64_t* counts, int n);
+
 /* Message of the last error on this context (static string if ctx is NULL). */
 const char* dg_cns_last_error(const dgcns_ctx* ctx);
 

@@ -27,7 +27,7 @@ class DGCNS:
 
     def __init__(self, ncells, lo, hi, periodic, k, nq_conv, nq_visc, *, gamma=1.4, Pr=0.71, Re=1600.0,
                  Ma=0.1, R=287.0, rho0=1.0, U0=1.0, L=1.0, u_mach=0.0, body_force=(0.0, 0.0, 0.0),
-                 precision=FP64, kernel=KERNEL_FUSED, mapping=MAP_AFFINE, map_param=0.0, geometry=0, device=None):
+                 precision=FP64, kernel=KERNEL_FACES, mapping=MAP_AFFINE, map_param=0.0, geometry=0, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libdgcns needs a CUDA device (there is no CPU fallback)")
         self.lib = _lib.load()
@@ -177,6 +177,21 @@ class DGCNS:
         c = ctypes.c_int64()
         self._check(self.lib.dg_cns_launch_count(self.ctx, ctypes.byref(c)))
         return c.value
+
+    def dg_cns_timing(self, enable):
+        """Start (clearing the totals) or stop per-kernel CUDA-event timing on the context's stream."""
+        self._check(self.lib.dg_cns_timing(self.ctx, 1 if enable else 0))
+
+    def dg_cns_kernel_times(self):
+        """{kind: (total ms, launches)} of the kernels timed since timing was enabled."""
+        n = len(_lib.KERNEL_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self._check(self.lib.dg_cns_kernel_times(self.ctx, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.KERNEL_KINDS) if cnt[i] > 0}
+
+    timing = dg_cns_timing
+    kernel_times = dg_cns_kernel_times
 
     def close(self):
         if getattr(self, "ctx", None):

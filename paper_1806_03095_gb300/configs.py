@@ -9,7 +9,7 @@ import math
 PI = math.pi
 
 
-def tgv(N, k, precision=0, kernel=1):
+def tgv(N, k, precision=0, kernel=2):
     return dict(name="tgv%d_k%d" % (N, k), ncells=(N, N, N), lo=(-PI,) * 3, hi=(PI,) * 3, periodic=(1, 1, 1),
                 k=k, nq_conv=(3 * k) // 2 + 1, nq_visc=k + 1, Re=1600.0, Ma=0.1, Pr=0.71, gamma=1.4, R=287.0,
                 u_mach=0.0, body_force=(0.0, 0.0, 0.0), mapping=0, map_param=0.0, precision=precision,
@@ -23,7 +23,7 @@ def channel_h_min(N, C=1.8):
     return min(y1 - y0, 2 * PI / N, PI / N)
 
 
-def channel(N=32, k=3, precision=1, kernel=1, mapping=1):
+def channel(N=32, k=3, precision=1, kernel=2, mapping=1):
     return dict(name="channel%d_k%d" % (N, k), ncells=(N, N, N), lo=(0.0, -1.0, 0.0), hi=(2 * PI, 1.0, PI),
                 periodic=(1, 0, 1), k=k, nq_conv=(3 * k) // 2 + 1, nq_visc=k + 1, Re=180.0, Ma=0.1, Pr=0.71,
                 gamma=1.4, R=287.0, u_mach=18.3, body_force=(1.0, 0.0, 0.0), mapping=mapping, map_param=1.8,

@@ -11,6 +11,7 @@
 // Y of the neighbour), so no two CTAs write the same cell.
 #pragma once
 #include "dg_adjoint_point.cuh"
+#include "dg_faces.cuh"
 #include "dg_launchers.h"
 
 namespace dgcns {
@@ -26,18 +27,24 @@ struct AdjSizes {
   static constexpr int ARENA = CELL > FACE ? CELL : FACE;
 };
 
-template <typename T, int N, int QC, int QV>
-constexpr int adj_cells_per_cta() {
+// PAIR: face terms come as shares from the face-centric adjoint face kernel (no neighbour states,
+// cell arena only).
+template <int N, int QC, int QV, bool PAIR>
+constexpr int adj_cell_elems() {
   using S = AdjSizes<N, QC, QV>;
-  constexpr int per_cell = (5 * 5 * S::N3 + S::ARENA) * (int)sizeof(T) + 16;
+  return PAIR ? 3 * 5 * S::N3 + S::CELL : 5 * 5 * S::N3 + S::ARENA;
+}
+
+template <typename T, int N, int QC, int QV, bool PAIR>
+constexpr int adj_cells_per_cta() {
+  constexpr int per_cell = adj_cell_elems<N, QC, QV, PAIR>() * (int)sizeof(T) + 16;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_cell;
   return cb < 1 ? 1 : (cb > 4 ? 4 : cb);
 }
 
-template <typename T, int N, int QC, int QV, int CB>
+template <typename T, int N, int QC, int QV, int CB, bool PAIR>
 constexpr size_t adj_smem_bytes() {
-  using S = AdjSizes<N, QC, QV>;
-  return (table_elems<N, QC, QV>() + (size_t)CB * (5 * 5 * S::N3 + S::ARENA) + CB) * sizeof(T) +
+  return (table_elems<N, QC, QV>() + (size_t)CB * adj_cell_elems<N, QC, QV, PAIR>() + CB) * sizeof(T) +
          2 * CB * sizeof(int) + 64;
 }
 
@@ -486,7 +493,7 @@ __device__ void adj_face_terms(const T* su, const T* sy, const T* snu, const T* 
 // Adjoint kernel.  Y = M^{-1} W for all cells (precomputed).  out_mode 0:
 // G = -(dF/dU)^T Y; out_mode 2: lam_U += dt * (-(dF/dU)^T Y) (RK stage adjoint).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int QC, int QV, int CB, int GEO>
+template <typename T, int N, int QC, int QV, int CB, int GEO, bool PAIR>
 __global__ void __launch_bounds__(NT) dg_adj_kernel(const KParams kp, const double* __restrict__ U,
                                                     const T* __restrict__ Y, T* __restrict__ G,
                                                     double* __restrict__ lamU) {
@@ -499,9 +506,9 @@ __global__ void __launch_bounds__(NT) dg_adj_kernel(const KParams kp, const doub
   T* sy = su + CB * 5 * N3;
   T* sg = sy + CB * 5 * N3;
   T* snu = sg + CB * 5 * N3;
-  T* sny = snu + CB * 5 * N3;
-  T* ar = sny + CB * 5 * N3;
-  T* tau_f = ar + CB * S::ARENA;
+  T* sny = snu + (PAIR ? 0 : CB * 5 * N3);
+  T* ar = sny + (PAIR ? 0 : CB * 5 * N3);
+  T* tau_f = ar + CB * (PAIR ? S::CELL : S::ARENA);
   int* wall = reinterpret_cast<int*>(tau_f + CB);
   int* nbi = wall + CB;
   const int e0 = blockIdx.x * CB;
@@ -519,6 +526,15 @@ __global__ void __launch_bounds__(NT) dg_adj_kernel(const KParams kp, const doub
   }
   __syncthreads();
   adj_cell_terms<T, N, QC, QV, CB, GEO>(su, sy, sg, ar, tb, kp, ph, e0, nb);
+  if constexpr (PAIR) {
+    static_assert(S::CELL >= fbuf_per_cell<N>(), "adjoint arena too small for face shares");
+    const T* F = static_cast<const T*>(kp.fbuf) + (size_t)e0 * fbuf_per_cell<N>();
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb * fbuf_per_cell<N>(); i += blockDim.x) ar[i] = F[i];
+    __syncthreads();
+    gather_face_shares<T, N>(sg, ar, tb, nb, CtaGroup());
+    __syncthreads();
+  } else {
   for (int d = 0; d < 3; ++d) {
     for (int s = 0; s < 2; ++s) {
       if (threadIdx.x < nb) {
@@ -554,6 +570,7 @@ __global__ void __launch_bounds__(NT) dg_adj_kernel(const KParams kp, const doub
       if (d == 2) adj_face_terms<T, N, QC, QV, CB, 2, GEO>(su, sy, snu, sny, wall, nbi, tau_f, sg, ar, tb, kp, ph, e0, nb, s);
     }
   }
+  }
   if (kp.out_mode == 2) {
     for (int i = threadIdx.x; i < nvals; i += blockDim.x) lamU[base + i] -= kp.dt * double(sg[i]);
   } else {
@@ -572,12 +589,12 @@ __global__ void dg_adj_prep_kernel(size_t n, double A, double B, const double* _
   }
 }
 
-template <typename T, int N, int QC, int QV, int GEO>
+template <typename T, int N, int QC, int QV, int GEO, bool PAIR>
 int adj_launch_geo(const KParams& kp, const double* U, const void* Y, void* G, double* lamU, cudaStream_t st) {
-  constexpr int CB = adj_cells_per_cta<T, N, QC, QV>();
-  constexpr size_t smem = adj_smem_bytes<T, N, QC, QV, CB>();
+  constexpr int CB = adj_cells_per_cta<T, N, QC, QV, PAIR>();
+  constexpr size_t smem = adj_smem_bytes<T, N, QC, QV, CB, PAIR>();
   if (smem > 227 * 1024) return -2;
-  auto k = dg_adj_kernel<T, N, QC, QV, CB, GEO>;
+  auto k = dg_adj_kernel<T, N, QC, QV, CB, GEO, PAIR>;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
@@ -594,8 +611,15 @@ int adj_launch(const KParams& kp, const double* U, const void* Y, void* G, doubl
   if constexpr (!F::adj || (sizeof(T) == 4 && !F::fp32)) {
     return -2;
   } else {
-    if (kp.gcc == nullptr) return adj_launch_geo<T, N, QC, QV, GEO_AFFINE>(kp, U, Y, G, lamU, st);
-    if constexpr (F::geo) return adj_launch_geo<T, N, QC, QV, GEO_STORED>(kp, U, Y, G, lamU, st);
+    if (kp.fbuf != nullptr) {
+      if constexpr (F::faces) {
+        if (kp.gcc == nullptr) return adj_launch_geo<T, N, QC, QV, GEO_AFFINE, true>(kp, U, Y, G, lamU, st);
+        if constexpr (F::geo) return adj_launch_geo<T, N, QC, QV, GEO_STORED, true>(kp, U, Y, G, lamU, st);
+      }
+      return -2;
+    }
+    if (kp.gcc == nullptr) return adj_launch_geo<T, N, QC, QV, GEO_AFFINE, false>(kp, U, Y, G, lamU, st);
+    if constexpr (F::geo) return adj_launch_geo<T, N, QC, QV, GEO_STORED, false>(kp, U, Y, G, lamU, st);
     return -2;
   }
 }

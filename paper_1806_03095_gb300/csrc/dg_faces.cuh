@@ -24,12 +24,14 @@ constexpr int fbuf_per_cell() {
 }
 
 // One face per item: own cell eo[b] (side s of its face), other cell en[b] (-1: wall, ghost state).
-// su/sn: own/other cell states [CB][5][N^3]; lc: [CB][5][N^2] scratch; fa: face arena.
+// lay: 4 trace layers [CB][5][N^2] (own values, own normal derivatives, other values, other normal
+// derivatives), read along the normal lines from global memory (the deviation state Ud when given,
+// else U - U_ref); lc: [CB][5][N^2] scratch; fa: face arena.
 template <typename T, int N, int QC, int QV, int CB, int d, int GEO, class G = CtaGroup>
-__device__ void face_pair_terms(const T* su, const T* sn, const int* eo, const int* en, const T* tau_f, T* fa, T* lc,
-                                const Tab<T>& tb, const KParams& kp, const PhysT<T>& ph, int nb, int s,
-                                T* __restrict__ FB, G grp = G(), const T* sx = nullptr, const T* sxn = nullptr,
-                                T* go = nullptr) {
+__device__ void face_pair_terms(const double* __restrict__ U, const T* __restrict__ Ud, const int* eo, const int* en,
+                                const T* tau_f, T* lay, T* fa, T* lc, const Tab<T>& tb, const KParams& kp,
+                                const PhysT<T>& ph, int nb, int s, T* __restrict__ FB, G grp = G(),
+                                const T* sx = nullptr, const T* sxn = nullptr, T* go = nullptr) {
   const int f = 2 * d + s, fo = 2 * d + (1 - s);
   constexpr int N2 = N * N, N3 = N * N * N;
   constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
@@ -41,21 +43,52 @@ __device__ void face_pair_terms(const T* su, const T* sn, const int* eo, const i
   const T* dlm = s ? tb.dl1 : tb.dl0;
   const T* dlp = s ? tb.dl0 : tb.dl1;
   const int nbl = nb * 5;
+  T* Lm = lay;  // own face values
+  T* Dm = Lm + CB * 5 * N2;  // own normal derivatives
+  T* Lp = Dm + CB * 5 * N2;  // other values
+  T* Dp = Lp + CB * 5 * N2;  // other normal derivatives
+
+  for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
+    const int ec = idx / N2, j = idx - ec * N2, e = ec / 5, c = ec - 5 * e;
+    const int j1 = j % N, j2 = j / N;
+    const double dref = c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0);
+    const size_t om = ((size_t)eo[e] * 5 + c) * N3;
+    T dn = T(0), vm = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int q = face_node<N>(d, i, j1, j2);
+      const T v = Ud ? Ud[om + q] : T(U[om + q] - dref);
+      dn += dlm[i] * v;
+      if (i == idm) vm = v;
+    }
+    Lm[idx] = vm;
+    Dm[idx] = dn;
+    if (en[e] < 0) {
+      Lp[idx] = T(0);
+      Dp[idx] = T(0);
+    } else {
+      const size_t op = ((size_t)en[e] * 5 + c) * N3;
+      T dq = T(0), vp = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int q = face_node<N>(d, i, j1, j2);
+        const T v = Ud ? Ud[op + q] : T(U[op + q] - dref);
+        dq += dlp[i] * v;
+        if (i == idp) vp = v;
+      }
+      Lp[idx] = vp;
+      Dp[idx] = dq;
+    }
+  }
+  grp.sync();
 
   if (kp.conv) {
     constexpr int P = QC * QC;
     if (GEO == GEO_FLY) fill_face_geo<T, N, QC, CB, d>(sx, s, fa, tb.eSc, tb.eDc, dlm, go, nb, grp);
-    T* Lm = fa;
-    T* Lp = Lm + CB * 5 * N2;
-    T* Tm = Lp + CB * 5 * N2;
+    T* Tm = fa;
     T* Tp = Tm + CB * 5 * QC * N;
     T* Um = Tp + CB * 5 * QC * N;
     T* Up = Um + CB * 5 * P;
-    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
-      const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
-      Lm[idx] = su[ec * N3 + face_node<N>(d, idm, j % N, j / N)];
-      Lp[idx] = en[e] < 0 ? T(0) : sn[ec * N3 + face_node<N>(d, idp, j % N, j / N)];
-    }
     grp.sync();
     sweep<T, 0, N, N, 1, QC, 1, false>(Lm, Tm, tb.eSc, nbl, grp);
     sweep<T, 0, N, N, 1, QC, 1, false>(Lp, Tp, tb.eSc, nbl, grp);
@@ -116,17 +149,13 @@ __device__ void face_pair_terms(const T* su, const T* sn, const int* eo, const i
   }
 
   constexpr int P = QV * QV;
-  T* Lm = fa;
-  T* Lp = Lm + CB * 5 * N2;
-  T* Dm = Lp + CB * 5 * N2;
-  T* Dp = Dm + CB * 5 * N2;
   if (kp.visc) {
     T* gnb = go + CB * 13 * P;  // GEO_FLY: the other side's face geometry
     if (GEO == GEO_FLY) {
       fill_face_geo<T, N, QV, CB, d>(sx, s, fa, tb.eSv, tb.eDv, dlm, go, nb, grp);
       fill_face_geo<T, N, QV, CB, d>(sxn, 1 - s, fa, tb.eSv, tb.eDv, dlp, gnb, nb, grp);
     }
-    T* Um = Dp + CB * 5 * N2;  // 8 point arrays [CB][5][P]
+    T* Um = fa;  // 8 point arrays [CB][5][P]
     T* Up = Um + CB * 5 * P;
     T* G1m = Up + CB * 5 * P;
     T* G2m = G1m + CB * 5 * P;
@@ -138,27 +167,6 @@ __device__ void face_pair_terms(const T* su, const T* sn, const int* eo, const i
     T* Tp = Tm + CB * 5 * N * QV;
     T* Tdm = Tp + CB * 5 * N * QV;
     T* Tdp = Tdm + CB * 5 * N * QV;
-    for (int idx = grp.rank(); idx < nbl * N2; idx += grp.size()) {
-      const int ec = idx / N2, j = idx - ec * N2, e = ec / 5;
-      const int j1 = j % N, j2 = j / N;
-      const T* um = su + ec * N3;
-      Lm[idx] = um[face_node<N>(d, idm, j1, j2)];
-      T dn = T(0);
-#pragma unroll
-      for (int i = 0; i < N; ++i) dn += dlm[i] * um[face_node<N>(d, i, j1, j2)];
-      Dm[idx] = dn;
-      if (en[e] < 0) {
-        Lp[idx] = T(0);
-        Dp[idx] = T(0);
-      } else {
-        const T* un = sn + ec * N3;
-        Lp[idx] = un[face_node<N>(d, idp, j1, j2)];
-        T dp = T(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) dp += dlp[i] * un[face_node<N>(d, i, j1, j2)];
-        Dp[idx] = dp;
-      }
-    }
     grp.sync();
     // values and normal derivatives of both traces to the face Gauss points
     sweep<T, 0, N, N, 1, QV, 1, false>(Lm, Tm, tb.eSv, nbl, grp);
@@ -313,13 +321,14 @@ __device__ void face_pair_terms(const T* su, const T* sn, const int* eo, const i
   }
 }
 
-// Face arena of face_pair_terms per face: conv: 2 layers, 2 tmp, 2 point arrays; visc: 4 layers,
-// 8 point arrays, 4 tmp.
+// Shared memory of face_pair_terms per face: 4 trace layers; arena: conv 2 tmp + 2 point arrays,
+// visc 8 point arrays + 4 tmp.
 template <int N, int QC, int QV>
 struct PairSizes {
   static constexpr int N2 = N * N;
-  static constexpr int CONV = 2 * 5 * N2 + 2 * 5 * QC * N + 2 * 5 * QC * QC;
-  static constexpr int VISC = 4 * 5 * N2 + 8 * 5 * QV * QV + 4 * 5 * N * QV;
+  static constexpr int LAYERS = 4 * 5 * N2;
+  static constexpr int CONV = 2 * 5 * QC * N + 2 * 5 * QC * QC;
+  static constexpr int VISC = 8 * 5 * QV * QV + 4 * 5 * N * QV;
   static constexpr int ARENA = CONV > VISC ? CONV : VISC;
 };
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "dg_adjoint.cuh"
+#include "dg_adjoint_faces.cuh"
 #include "dg_faces.cuh"
 #include "dg_kernels.cuh"
 #include "dg_launchers.h"
@@ -937,16 +938,19 @@ template <typename T, int N, int QC, int QV, int CB, int GEO>
 constexpr size_t face_smem_bytes() {
   using S = Sizes<N, QC, QV>;
   const size_t geo = GEO == GEO_FLY ? (size_t)CB * (2 * 3 * S::N3 + S::FLY_OUT) : 0;
-  const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * 5 * S::N3 * 2 + (size_t)CB * 5 * S::N2 +
-                       face_arena_elems<T, N, QC, QV, CB, GEO>() + geo + CB;
+  const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * PairSizes<N, QC, QV>::LAYERS +
+                       (size_t)CB * 5 * S::N2 + face_arena_elems<T, N, QC, QV, CB, GEO>() + geo + CB;
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
 }
 
 // Faces per CTA: the largest batch (<= 8) below ~112 KB of shared memory.
-template <typename T, int N, int QC, int QV>
+template <typename T, int N, int QC, int QV, int GEO>
 constexpr int faces_per_cta() {
   using S = Sizes<N, QC, QV>;
-  constexpr int per_face = (2 * 5 * S::N3 + 5 * S::N2 + PairSizes<N, QC, QV>::ARENA) * (int)sizeof(T) + 16;
+  constexpr int arena = GEO == GEO_FLY && S::FLY_TMP > PairSizes<N, QC, QV>::ARENA ? S::FLY_TMP
+                                                                                    : PairSizes<N, QC, QV>::ARENA;
+  constexpr int geo = GEO == GEO_FLY ? 2 * 3 * S::N3 + S::FLY_OUT : 0;
+  constexpr int per_face = (PairSizes<N, QC, QV>::LAYERS + 5 * S::N2 + arena + geo) * (int)sizeof(T) + 16;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_face;
   return cb < 1 ? 1 : (cb > 8 ? 8 : cb);
 }
@@ -958,9 +962,8 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams 
   constexpr int N3 = S::N3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stab = reinterpret_cast<T*>(smem_raw);
-  T* su = stab + table_elems<N, QC, QV>();
-  T* sn = su + CB * 5 * N3;
-  T* lc = sn + CB * 5 * N3;
+  T* lay = stab + table_elems<N, QC, QV>();
+  T* lc = lay + CB * PairSizes<N, QC, QV>::LAYERS;
   T* fa = lc + CB * 5 * S::N2;
   T* sx = fa + face_arena_elems<T, N, QC, QV, CB, GEO>();  // GEO_FLY only
   T* sxn = sx + CB * 3 * N3;
@@ -1016,15 +1019,6 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams 
   }
   __syncthreads();
   const T* Ud = static_cast<const T*>(kp.Udev);
-  for (int i = threadIdx.x; i < nb * 5 * N3; i += blockDim.x) {
-    const int b = i / (5 * N3), r = i - b * 5 * N3;
-    const size_t so = (size_t)eo[b] * 5 * N3 + r;
-    su[i] = Ud ? Ud[so] : T(U[so] - ref_of(kp, r / N3));
-    if (en[b] >= 0) {
-      const size_t sq = (size_t)en[b] * 5 * N3 + r;
-      sn[i] = Ud ? Ud[sq] : T(U[sq] - ref_of(kp, r / N3));
-    }
-  }
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT);
     for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) {
@@ -1036,18 +1030,18 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams 
   __syncthreads();
   const CtaGroup cg;
   if (d == 0)
-    face_pair_terms<T, N, QC, QV, CB, 0, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
   else if (d == 1)
-    face_pair_terms<T, N, QC, QV, CB, 1, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
   else
-    face_pair_terms<T, N, QC, QV, CB, 2, GEO>(su, sn, eo, en, tau_f, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
 }
 
 template <typename T, int N, int QC, int QV, int GEO>
 int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) {
-  constexpr int CB = faces_per_cta<T, N, QC, QV>();
+  constexpr int CB = faces_per_cta<T, N, QC, QV, GEO>();
   constexpr size_t smem = face_smem_bytes<T, N, QC, QV, CB, GEO>();
-  if (smem > 227 * 1024) return -2;
+  static_assert(smem <= 227 * 1024, "face kernel shared memory");
   auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
   static bool attr = false;
   if (!attr) {
@@ -1108,8 +1102,11 @@ void fill_launchers(Launchers& L) {
     L.prep_fp32 = adj_prep_launch<float>;
   } else if constexpr (PART == 4) {  // face-centric face kernel, FP64
     L.faces_fp64 = faces_dispatch<double, N, QC, QV>;
-  } else {  // face-centric face kernel, FP32
+  } else if constexpr (PART == 5) {  // face-centric face kernel, FP32
     L.faces_fp32 = faces_dispatch<float, N, QC, QV>;
+  } else {  // face-centric adjoint face kernels
+    L.adj_faces_fp64 = adj_faces_dispatch<double, N, QC, QV>;
+    L.adj_faces_fp32 = adj_faces_dispatch<float, N, QC, QV>;
   }
 }
 

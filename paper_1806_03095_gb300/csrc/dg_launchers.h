@@ -19,6 +19,8 @@ using GeomFn = int (*)(const KParams&, const double* xyz, double* gcc, double* g
 
 // Adjoint: G = -(dF/dU)^T Y (lamU == nullptr) or lamU += dt * that (out_mode 2 in kp).
 using AdjFn = int (*)(const KParams&, const double* U, const void* Y, void* G, double* lamU, cudaStream_t);
+// Face-centric adjoint face kernel: shares of (dF/dU)^T Y of every face into FB.
+using AdjFaceFn = int (*)(const KParams&, const double* U, const void* Y, void* FB, cudaStream_t);
 using PrepFn = int (*)(size_t n, double A, double B, const double* lamU, void* lamdU, void* W, cudaStream_t);
 // Face-centric face integrals: the face shares of every cell into FB ([Nc][6][2][5][N^2]).
 using FaceFn = int (*)(const KParams&, const double* U, void* FB, cudaStream_t);
@@ -37,7 +39,7 @@ struct Feat {
   static constexpr bool geo = rule && (N == 3 || N == 4 || N == 6);    // k = 2, 3, 5
   static constexpr bool fly = rule && N == 4;                          // k = 3
   static constexpr bool adj = rule && (N == 3 || N == 4 || N == 5);    // k = 2, 3, 4
-  static constexpr bool faces = rule;
+  static constexpr bool faces = true;
   static constexpr int bits = (fp32 ? FEAT_FP32 : 0) | (geo ? FEAT_GEO : 0) | (fly ? FEAT_FLY : 0) |
                               (adj ? FEAT_ADJ : 0) | (faces ? FEAT_FACES : 0);
 };
@@ -49,6 +51,7 @@ struct Launchers {
   DiagFn diag_fp64, diag_fp32;
   GeomFn geom;
   AdjFn adj_fp64, adj_fp32;
+  AdjFaceFn adj_faces_fp64, adj_faces_fp32;
   PrepFn prep_fp64, prep_fp32;
   EkGradFn ekgrad;
   int (*dev_fp32)(const KParams&, const double* U, void* D, cudaStream_t);  // D = float(U - U_ref)
@@ -70,15 +73,16 @@ struct Launchers {
   X(6, 6, 6)
 
 // Parts of each instantiation (separate translation units): FP64 operator, FP32 operator,
-// diagnostics + geometry, adjoint, FP64 face kernel, FP32 face kernel.
-#define DGCNS_PARTS 6
+// diagnostics + geometry, adjoint, FP64 face kernel, FP32 face kernel, adjoint face kernels.
+#define DGCNS_PARTS 7
 #define DGCNS_DECLARE(N, QC, QV)                     \
   void launchers_##N##_##QC##_##QV##_0(Launchers&); \
   void launchers_##N##_##QC##_##QV##_1(Launchers&); \
   void launchers_##N##_##QC##_##QV##_2(Launchers&); \
   void launchers_##N##_##QC##_##QV##_3(Launchers&); \
   void launchers_##N##_##QC##_##QV##_4(Launchers&); \
-  void launchers_##N##_##QC##_##QV##_5(Launchers&);
+  void launchers_##N##_##QC##_##QV##_5(Launchers&); \
+  void launchers_##N##_##QC##_##QV##_6(Launchers&);
 DGCNS_CONFIGS(DGCNS_DECLARE)
 #undef DGCNS_DECLARE
 

@@ -236,7 +236,8 @@ struct Registry {
 #define DGCNS_ENTRY(N, QC, QV)                                                                           \
   {N, QC, QV,                                                                                            \
    {&launchers_##N##_##QC##_##QV##_0, &launchers_##N##_##QC##_##QV##_1, &launchers_##N##_##QC##_##QV##_2, \
-    &launchers_##N##_##QC##_##QV##_3, &launchers_##N##_##QC##_##QV##_4, &launchers_##N##_##QC##_##QV##_5}},
+    &launchers_##N##_##QC##_##QV##_3, &launchers_##N##_##QC##_##QV##_4, &launchers_##N##_##QC##_##QV##_5, \
+    &launchers_##N##_##QC##_##QV##_6}},
 const Registry kRegistry[] = {DGCNS_CONFIGS(DGCNS_ENTRY)};
 #undef DGCNS_ENTRY
 
@@ -267,6 +268,16 @@ struct dgcns_ctx {
   double* d_partial = nullptr;
   int diag_blocks = 0;
   int64_t launches = 0;
+  // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double kt_ms[DGCNS_KT_COUNT] = {};
+  int64_t kt_n[DGCNS_KT_COUNT] = {};
   double volume = 0.0;  // domain volume (Gauss sum at the convective points)
   std::string err;
 };
@@ -602,6 +613,11 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_dev);
   cudaFree(c->d_fb);
   cudaFree(c->d_xyz);
+  for (const auto& t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFree(c->d_partial);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
@@ -636,9 +652,67 @@ int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {
   return DGCNS_OK;
 }
 
+// Per-kernel timing: an event before and after each launch on the context's stream (RAII scope).
+static cudaEvent_t take_event(dgcns_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct TimedScope {
+  dgcns_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  TimedScope(dgcns_ctx* c_, int k) : c(c_), kind(k) {
+    if (c->timing && (a = take_event(c)) != nullptr) cudaEventRecord(a, c->stream);
+  }
+  ~TimedScope() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) {
+      c->pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({kind, a, b});
+  }
+};
+
+static int flush_times(dgcns_ctx* c) {
+  if (c->pending.empty()) return DGCNS_OK;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "timing synchronize");
+  for (const auto& t : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      c->kt_ms[t.kind] += ms;
+      c->kt_n[t.kind] += 1;
+    }
+    c->pool.push_back(t.a);
+    c->pool.push_back(t.b);
+  }
+  c->pending.clear();
+  return DGCNS_OK;
+}
+
+static int op_kind(int mode) {
+  switch (mode) {
+    case OP_CELL: return DGCNS_KT_CELL;
+    case OP_FACE: return DGCNS_KT_FACE;
+    case OP_MASS: return DGCNS_KT_MASS;
+    case OP_CELL | OP_MASS: return DGCNS_KT_CELL_STAGE;
+    default: return DGCNS_KT_FUSED;
+  }
+}
+
 static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const void* Rin, void* Rout, void* dU,
                   double* Uout) {
   const OpFn f = c->prm.precision == DGCNS_MIXED ? c->L.op_fp32 : c->L.op_fp64;
+  TimedScope ts(c, op_kind(mode));
   const int r = f(mode, kp, U, Rin, Rout, dU, Uout, c->stream);
   c->launches += 1;
   if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "operator variant not compiled or too large for shared memory");
@@ -650,6 +724,7 @@ static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const voi
 // follows adds them (kp.fbuf).
 static int run_faces(dgcns_ctx* c, KParams& kp, const double* U) {
   const FaceFn f = c->prm.precision == DGCNS_MIXED ? c->L.faces_fp32 : c->L.faces_fp64;
+  TimedScope ts(c, DGCNS_KT_FACES);
   const int r = f(kp, U, c->d_fb, c->stream);
   c->launches += 1;
   if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "face kernel not compiled or too large for shared memory");
@@ -663,6 +738,7 @@ static int run_faces(dgcns_ctx* c, KParams& kp, const double* U) {
 // operator evaluation (an elementwise pass) so that the operator kernels do no FP64 conversions.
 static int prep_dev(dgcns_ctx* c, KParams& kp, const double* U) {
   if (!c->d_dev || !U) return DGCNS_OK;
+  TimedScope ts(c, DGCNS_KT_DEV);
   if (c->L.dev_fp32(kp, U, c->d_dev, c->stream) != 0) return cuda_fail(c, "deviation pre-pass");
   c->launches += 1;
   kp.Udev = c->d_dev;
@@ -763,6 +839,26 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
   return DGCNS_OK;
 }
 
+// Adjoint VJP kernel(s) for Y in d_R: the face-centric organisation first writes the face shares.
+static int run_adj(dgcns_ctx* c, KParams ka, const double* U, void* G, double* lam_U) {
+  if (c->prm.kernel == DGCNS_KERNEL_FACES) {
+    const AdjFaceFn ff = c->prm.precision == DGCNS_MIXED ? c->L.adj_faces_fp32 : c->L.adj_faces_fp64;
+    TimedScope ts(c, DGCNS_KT_ADJ_FACES);
+    const int rf = ff(ka, U, c->d_R, c->d_fb, c->stream);
+    c->launches += 1;
+    if (rf == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint face kernel not compiled for this (k, nq)");
+    if (rf) return cuda_fail(c, "adjoint face kernel launch");
+    ka.fbuf = c->d_fb;
+  }
+  const AdjFn f = c->prm.precision == DGCNS_MIXED ? c->L.adj_fp32 : c->L.adj_fp64;
+  TimedScope ts(c, DGCNS_KT_ADJ);
+  const int ra = f(ka, U, c->d_R, G, lam_U, c->stream);
+  c->launches += 1;
+  if (ra == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint kernel does not fit shared memory for this (k, nq)");
+  if (ra) return cuda_fail(c, "adjoint kernel launch");
+  return DGCNS_OK;
+}
+
 int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (!U || !W || !G) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
@@ -776,12 +872,7 @@ int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) 
   if (r) return r;
   KParams ka = c->kp;
   ka.out_mode = 0;
-  const AdjFn f = c->prm.precision == DGCNS_MIXED ? c->L.adj_fp32 : c->L.adj_fp64;
-  const int ra = f(ka, U, c->d_R, G, nullptr, c->stream);
-  c->launches += 1;
-  if (ra == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint kernel does not fit shared memory for this (k, nq)");
-  if (ra) return cuda_fail(c, "adjoint kernel launch");
-  return DGCNS_OK;
+  return run_adj(c, ka, U, G, nullptr);
 }
 
 int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_in, double* lam_U, void* lam_dU) {
@@ -794,8 +885,11 @@ int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_
   if ((const void*)lam_U == (const void*)U_in) return fail(c, DGCNS_ERR_INVALID_ARG, "lam_U must not alias U_in");
   const PrepFn prep = c->prm.precision == DGCNS_MIXED ? c->L.prep_fp32 : c->L.prep_fp64;
   // W = lam_dU + B lam_U (scratch), lam_dU <- A W
-  if (prep(c->state_elems, RK_A[stage], RK_B[stage], lam_U, lam_dU, c->d_R, c->stream) != 0)
-    return cuda_fail(c, "adjoint stage preparation");
+  {
+    TimedScope ts(c, DGCNS_KT_ADJ_PREP);
+    if (prep(c->state_elems, RK_A[stage], RK_B[stage], lam_U, lam_dU, c->d_R, c->stream) != 0)
+      return cuda_fail(c, "adjoint stage preparation");
+  }
   c->launches += 1;
   KParams km = c->kp;
   km.out_mode = 0;
@@ -805,12 +899,7 @@ int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_
   KParams ka = c->kp;
   ka.out_mode = 2;
   ka.dt = dt;
-  const AdjFn f = c->prm.precision == DGCNS_MIXED ? c->L.adj_fp32 : c->L.adj_fp64;
-  const int ra = f(ka, U_in, c->d_R, nullptr, lam_U, c->stream);
-  c->launches += 1;
-  if (ra == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint kernel does not fit shared memory for this (k, nq)");
-  if (ra) return cuda_fail(c, "adjoint kernel launch");
-  return DGCNS_OK;
+  return run_adj(c, ka, U_in, nullptr, lam_U);
 }
 
 int dg_cns_kinetic_energy_gradient(dgcns_ctx* c, const double* U, double* G) {
@@ -822,6 +911,7 @@ int dg_cns_kinetic_energy_gradient(dgcns_ctx* c, const double* U, double* G) {
     kp.gcc = c->g64[0];
     kp.gm = c->g64[4];
   }
+  TimedScope ts(c, DGCNS_KT_OTHER);
   const int r = c->L.ekgrad(kp, U, G, 1.0 / c->volume, c->stream);
   c->launches += 1;
   if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "kinetic-energy gradient does not fit shared memory");
@@ -848,7 +938,10 @@ int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* ou
   KParams kp = diag_params(c);
   int nblk = 0;
   const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
-  if (f(kp, U, LU, c->d_partial, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics kernel launch");
+  {
+    TimedScope ts(c, DGCNS_KT_OTHER);
+    if (f(kp, U, LU, c->d_partial, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics kernel launch");
+  }
   c->launches += 1;
   std::vector<double> part((size_t)nblk * 10);
   if (cudaMemcpyAsync(part.data(), c->d_partial, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
@@ -944,6 +1037,32 @@ int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, do
 int dg_cns_launch_count(const dgcns_ctx* c, int64_t* count) {
   if (!c || !count) return DGCNS_ERR_INVALID_ARG;
   *count = c->launches;
+  return DGCNS_OK;
+}
+
+int dg_cns_timing(dgcns_ctx* c, int enable) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  const int r = flush_times(c);
+  if (r) return r;
+  if (enable) {
+    for (int i = 0; i < DGCNS_KT_COUNT; ++i) {
+      c->kt_ms[i] = 0.0;
+      c->kt_n[i] = 0;
+    }
+  }
+  c->timing = enable != 0;
+  return DGCNS_OK;
+}
+
+int dg_cns_kernel_times(dgcns_ctx* c, double* ms, int64_t* counts, int n) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (n < 0 || n > DGCNS_KT_COUNT) return fail(c, DGCNS_ERR_INVALID_ARG, "n must be 0..DGCNS_KT_COUNT");
+  const int r = flush_times(c);
+  if (r) return r;
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = c->kt_ms[i];
+    if (counts) counts[i] = c->kt_n[i];
+  }
   return DGCNS_OK;
 }
 

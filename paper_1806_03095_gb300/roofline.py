@@ -12,6 +12,7 @@ PT_CELL_CONV = 62      # 1/rho, pressure, 3 directional fluxes, contravariant sc
 PT_CELL_VISC = 150     # velocity/temperature gradients, stress, energy flux, scaling
 PT_FACE_CONV = 110     # both traces: 1/rho, pressure, wave speed; LLF combination
 PT_FACE_VISC = 420     # F_v on both sides, F_v(U-, [[U]] (x) n), penalty, scaling
+PT_FACE_VISC_PAIR = 520  # face-centric: + F_v(U+, [[U]] (x) n) for the other cell
 PT_MASS = 1
 
 
@@ -51,6 +52,58 @@ def face_flops(N, QC, QV):
     f += 5 * N * N * N * 2                               # scatter along the normal lines
     f += PT_FACE_VISC * QV * QV
     return f
+
+
+def face_pair_flops(N, QC, QV):
+    """One interior face evaluated once for both cells (face-centric kernel): shared traces and fluxes, the
+    convective share of the other cell is a negation, the viscous tests are done per side."""
+    f = 0
+    f += 5 * 2 * (_sweep(N, N, QC) + _sweep(QC, N, QC))      # both traces
+    f += 5 * (_sweep(QC, QC, N) + _sweep(N, QC, N))          # one test
+    f += PT_FACE_CONV * QC * QC
+    interp_v = _sweep(N, N, QV) + _sweep(QV, N, QV)
+    f += 5 * 2 * N * N * 2 * N                               # normal derivatives, both sides
+    f += 5 * 4 * interp_v                                    # values and normal derivatives, both sides
+    f += 5 * 4 * _sweep(QV, QV, QV)                          # tangential collocation derivatives, both sides
+    f += 2 * 5 * 2 * _sweep(QV, QV, QV)                      # tangential gradient tests, both sides
+    f += 2 * 5 * 2 * (_sweep(QV, QV, N) + _sweep(N, QV, N))  # value and normal-gradient tests, both sides
+    f += PT_FACE_VISC_PAIR * QV * QV
+    return f
+
+
+def gather_flops(N):
+    """Adding the 6 face shares of a cell (value layer + normal-gradient coefficients along the normal lines)."""
+    return 5 * N ** 3 * 6 * 3
+
+
+def cell_stage_flops_per_cell(N, QC, QV):
+    """Face-centric cell kernel: cell integrals + face shares + inverse mass + update."""
+    return cell_flops(N, QC, QV) + gather_flops(N) + mass_flops(N) + 4 * 5 * N ** 3
+
+
+def kernel_flops(kind, N, QC, QV, Nc):
+    """Algorithmic flops of one launch of a kernel kind (names of dg_cns_kernel_times) on a periodic mesh of
+    Nc cells (3 Nc faces)."""
+    per = {"fused": stage_flops_per_cell(N, QC, QV) * Nc,
+           "faces": face_pair_flops(N, QC, QV) * 3 * Nc,
+           "cell_stage": cell_stage_flops_per_cell(N, QC, QV) * Nc,
+           "cell": cell_flops(N, QC, QV) * Nc,
+           "face": 6 * face_flops(N, QC, QV) * Nc,
+           "mass": (mass_flops(N) + 4 * 5 * N ** 3) * Nc}
+    return per.get(kind)
+
+
+def kernel_bytes(kind, N, Nc, rbytes):
+    """Algorithmic HBM bytes of one launch (stages 1..4: dU read): U in FP64, residual-type dU and face shares."""
+    nodes = Nc * N ** 3
+    shares = 60 * N * N * Nc * rbytes
+    per = {"fused": nodes * stage_bytes_per_node(rbytes),
+           "faces": nodes * 5 * 8 + shares,
+           "cell_stage": nodes * stage_bytes_per_node(rbytes) + shares,
+           "cell": nodes * 5 * (8 + rbytes),
+           "face": nodes * 5 * (8 + 2 * rbytes),
+           "mass": nodes * stage_bytes_per_node(rbytes) - nodes * 5 * 8 + nodes * 5 * rbytes}
+    return per.get(kind)
 
 
 def mass_flops(N):

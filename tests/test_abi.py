@@ -77,6 +77,15 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dg_cns_rk_stage(None, 0, 1.0, 0.0, None, None, None) == -1
     c = ctypes.c_int64()
     assert lib.dg_cns_launch_count(None, ctypes.byref(c)) == -1
+    assert lib.dg_cns_timing(None, 1) == -1
+    assert lib.dg_cns_kernel_times(None, None, None, 0) == -1
+
+
+def test_kernel_kinds_match_header():
+    text = open(os.path.join(ROOT, "include", "dgcns.h")).read()
+    kinds = dict((name.lower(), int(v)) for name, v in re.findall(r"#define DGCNS_KT_(\w+) (\d+)", text))
+    assert kinds.pop("count") == len(_lib.KERNEL_KINDS)
+    assert sorted(kinds, key=kinds.get) == list(_lib.KERNEL_KINDS)
 
 
 def test_library_is_in_tree():

@@ -28,10 +28,11 @@ def rel(a, b):
 
 
 def pair(ncells, k, mapping=0, param=0.0, periodic=(1, 1, 1), lo=(-PI,) * 3, hi=(PI,) * 3, precision=0,
-         Re=1600.0, u_mach=0.0):
+         Re=1600.0, u_mach=0.0, kernel=1):
+    """kernel 1: element-centric adjoint kernel; kernel 2: face-centric adjoint face kernel + cell kernel."""
     qc, qv = (3 * k) // 2 + 1, k + 1
     g = DGCNS(ncells, lo, hi, periodic, k, qc, qv, Re=Re, u_mach=u_mach, precision=precision, mapping=mapping,
-              map_param=param)
+              map_param=param, kernel=kernel)
     mesh = BoxMesh(ncells, lo, hi, periodic, k, mapping, param)
     return g, DGOperator(mesh, ph.Physics.from_numbers(Re, 0.71, 0.1, u_mach=(u_mach or None)), qc, qv)
 
@@ -41,18 +42,20 @@ def oracle_vjp(op, U, W):
     return torch.autograd.grad(op.L(Ur), Ur, W)[0]
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("k", [2, 3])
-def test_adjoint_apply_matches_oracle_vjp(k):
-    g, op = pair((2, 2, 3), k)
+def test_adjoint_apply_matches_oracle_vjp(k, kernel):
+    g, op = pair((2, 2, 3), k, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 60 + k)
     W = inputs.uniform(U.shape, 61 + k)
     l2, mx = rel(g.adjoint_apply(U.cuda(), W.cuda()), oracle_vjp(op, U, W))
     assert l2 < 1e-12 and mx < 1e-12, (l2, mx)
 
 
-def test_adjoint_dot_product_identity_with_oracle_tlm():
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_dot_product_identity_with_oracle_tlm(kernel):
     """<W, J V> (oracle forward mode) = <J^T W, V> (CUDA adjoint)."""
-    g, op = pair((2, 2, 2), 3)
+    g, op = pair((2, 2, 2), 3, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 70)
     V = inputs.uniform(U.shape, 71)
     W = inputs.uniform(U.shape, 72)
@@ -62,33 +65,48 @@ def test_adjoint_dot_product_identity_with_oracle_tlm():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def test_adjoint_apply_walls():
-    g, op = pair((2, 3, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3)
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_apply_walls(kernel):
+    g, op = pair((2, 3, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
+                 kernel=kernel)
     U = inputs.channel_state(g.node_coords().cpu(), 5)
     W = inputs.uniform(U.shape, 73)
     l2, mx = rel(g.adjoint_apply(U.cuda(), W.cuda()), oracle_vjp(op, U, W))
     assert l2 < 1e-11 and mx < 1e-11, (l2, mx)
 
 
-def test_adjoint_apply_deformed_mesh():
-    g, op = pair((2, 2, 2), 3, mapping=2, param=0.05)
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_apply_walls_on_every_side(kernel):
+    """Walls on all six sides of a ragged 3x2x4 box (lower-wall faces of the face-centric kernel)."""
+    g, op = pair((3, 2, 4), 2, periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1.5, 1.0, 2.0), Re=180.0, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 78)
+    W = inputs.uniform(U.shape, 79)
+    l2, mx = rel(g.adjoint_apply(U.cuda(), W.cuda()), oracle_vjp(op, U, W))
+    assert l2 < 1e-11 and mx < 1e-11, (l2, mx)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_apply_deformed_mesh(kernel):
+    g, op = pair((2, 2, 2), 3, mapping=2, param=0.05, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 74)
     W = inputs.uniform(U.shape, 75)
     l2, mx = rel(g.adjoint_apply(U.cuda(), W.cuda()), oracle_vjp(op, U, W))
     assert l2 < 1e-12 and mx < 1e-12, (l2, mx)
 
 
-def test_adjoint_apply_mixed_precision():
-    g, op = pair((2, 2, 2), 3, precision=1)
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_apply_mixed_precision(kernel):
+    g, op = pair((2, 2, 2), 3, precision=1, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 76)
     W = inputs.uniform(U.shape, 77)
     l2, mx = rel(g.adjoint_apply(U.cuda(), W.float().cuda()), oracle_vjp(op, U, W))
     assert l2 < 1e-4 and mx < 1e-3, (l2, mx)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("stage", [0, 3])
-def test_rk_stage_adjoint_matches_oracle(stage):
-    g, op = pair((2, 2, 2), 2)
+def test_rk_stage_adjoint_matches_oracle(stage, kernel):
+    g, op = pair((2, 2, 2), 2, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 80)
     dU = 1e-2 * inputs.uniform(U.shape, 81)
     lamU = inputs.uniform(U.shape, 82)
@@ -137,8 +155,8 @@ def control_to_state(u0, rho, T0, cv):
     return torch.cat([rho[:, None], m, rhoE[:, None]], 1)
 
 
-def _setup_tgv_adjoint(N=4, k=4):
-    g, op = pair((N, N, N), k)
+def _setup_tgv_adjoint(N=4, k=4, kernel=1):
+    g, op = pair((N, N, N), k, kernel=kernel)
     U0 = inputs.tgv_state(op.xyz)
     rho = U0[:, 0].clone()
     u0 = U0[:, 1:4] / rho[:, None]
@@ -147,10 +165,15 @@ def _setup_tgv_adjoint(N=4, k=4):
     return g, op, rho, u0, T0, cv
 
 
-def test_full_adjoint_gradient_vs_oracle_tlm_and_fd():
+_TLM_CACHE = {}
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_full_adjoint_gradient_vs_oracle_tlm_and_fd(kernel):
     """TGV 4^3, k = 4: 6 RK(5,4) steps with checkpoints every 2 steps; gradient of the final kinetic energy
-    with respect to the initial velocity field, along 8 seeded unit directions."""
-    g, op, rho, u0, T0, cv = _setup_tgv_adjoint()
+    with respect to the initial velocity field, along 8 seeded unit directions (the oracle's directional
+    derivatives are computed once and reused for both kernel organisations)."""
+    g, op, rho, u0, T0, cv = _setup_tgv_adjoint(kernel=kernel)
     dt = 2e-3
     nsteps, every = 6, 2
     rho_g, u0_g = rho.cuda(), u0.cuda().requires_grad_(True)
@@ -178,7 +201,9 @@ def test_full_adjoint_gradient_vs_oracle_tlm_and_fd():
     for i in range(8):
         v = inputs.random_direction(u0.shape, 1806 + i)
         dJ = float((grad * v).sum())
-        tlm = float(jvp(J_oracle, (u0,), (v,))[1])
+        if i not in _TLM_CACHE:
+            _TLM_CACHE[i] = float(jvp(J_oracle, (u0,), (v,))[1])
+        tlm = _TLM_CACHE[i]
         assert abs(dJ - tlm) <= 1e-10 * gnorm, (i, dJ, tlm, gnorm)
         fd = (J_gpu(u0 + h * v) - J_gpu(u0 - h * v)) / (2 * h)
         assert abs(dJ - fd) <= 1e-6 * gnorm, (i, dJ, fd, gnorm)
