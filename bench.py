@@ -34,6 +34,28 @@ FP64_PEAK_TFLOPS = 1.2   # measured FP64 FMA throughput of this machine's GB300 (FM
 FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per cell and launch from one ncu capture of
+# a kernel kind on a TGV mesh larger than L2, with the digest of the library sources it was built from:
+# (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
+# The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
+TRAFFIC = {
+    ("faces", 0, 4, 5, 4): (15115.0, "6236133f09abd832d243a8d96f46039ed1e80a8e318bddd5382406d696191926",
+                            "profiles/dg_face_kernel_fp64_tgv48_k3_full.md"),
+    ("cell_stage", 0, 4, 5, 4): (17690.0, "6236133f09abd832d243a8d96f46039ed1e80a8e318bddd5382406d696191926",
+                                 "profiles/dg_op_kernel_cell_stage_fp64_tgv48_k3_full.md"),
+}
+
+
+def traffic_per_launch(kind, prec, N, QC, QV, Nc):
+    entry = TRAFFIC.get((kind, prec, N, QC, QV))
+    if entry is None:
+        return None, None
+    from paper_1806_03095_gb300 import build
+    if build._sources_digest() != entry[1]:
+        return None, entry[2] + " (kernel sources changed since the capture)"
+    return entry[0] * Nc, entry[2]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -271,8 +293,9 @@ def roofline_entry(ktimes, cfg, prec, peaks):
     fl = roofline.kernel_flops(dom, N, QC, QV, Nc) or 0.0
     by = kernels[dom].get("hbm_gbs", 0.0) * 1e9 * t
     ach = fl / t / 1e12
+    traffic, traffic_src = traffic_per_launch(dom, prec, N, QC, QV, Nc)
     return {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-            "traffic": None,
+            "traffic": traffic, "traffic_source": traffic_src,
             "peak_source": "measured %s FMA probe (no %s entry in MEASURED_PEAKS.json)"
             % ("FP32" if prec else "FP64", "FP32" if prec else "FP64"),
             "kernel": KERNEL_NAMES.get(dom, dom), "avg_launch_ms": round(kms / n, 4), "flops_per_launch": fl,

@@ -1037,26 +1037,136 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams 
     face_pair_terms<T, N, QC, QV, CB, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
 }
 
+// Warp-per-face organisation of the same face kernel (used for the FP32 form, as the warp-per-cell
+// cell kernel): WPC warps per CTA, each warp takes one face through every phase with warp barriers.
+template <typename T, int N, int QC, int QV, int GEO>
+constexpr int face_warp_slice_elems() {
+  using S = Sizes<N, QC, QV>;
+  const int geo = GEO == GEO_FLY ? 2 * 3 * S::N3 + S::FLY_OUT : 0;
+  const int e = PairSizes<N, QC, QV>::LAYERS + 5 * S::N2 + (int)face_arena_elems<T, N, QC, QV, 1, GEO>() + geo + 1 +
+                2 * 8 / (int)sizeof(T) + 2;
+  return (e + 7) & ~7;
+}
+
+template <typename T, int N, int QC, int QV, int WPC, int GEO>
+constexpr size_t face_warp_smem_bytes() {
+  return ((size_t)table_elems<N, QC, QV>() + (size_t)WPC * face_warp_slice_elems<T, N, QC, QV, GEO>()) * sizeof(T) +
+         64;
+}
+
+template <typename T, int N, int QC, int QV, int WPC, int GEO>
+__global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp, const double* __restrict__ U,
+                                                                T* __restrict__ FB) {
+  using S = Sizes<N, QC, QV>;
+  constexpr int N3 = S::N3;
+  constexpr int SL = face_warp_slice_elems<T, N, QC, QV, GEO>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stab = reinterpret_cast<T*>(smem_raw);
+  const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  const int d = blockIdx.y;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const int nstd = (kp.Nc + WPC - 1) / WPC;
+  int s, i;
+  if ((int)blockIdx.x < nstd) {
+    s = 1;
+    i = blockIdx.x * WPC + w;
+    if (i >= kp.Nc) return;  // only warp barriers below
+  } else {
+    if (kp.periodic[d]) return;
+    s = 0;
+    i = (blockIdx.x - nstd) * WPC + w;
+    if (i >= kp.nc[t1] * kp.nc[t2]) return;
+  }
+  const WarpGroup grp;
+  T* lay = stab + table_elems<N, QC, QV>() + w * SL;
+  T* lc = lay + PairSizes<N, QC, QV>::LAYERS;
+  T* fa = lc + 5 * S::N2;
+  T* sx = fa + face_arena_elems<T, N, QC, QV, 1, GEO>();  // GEO_FLY only
+  T* sxn = sx + 3 * N3;
+  T* go = sxn + 3 * N3;
+  T* tau_f = sx + (GEO == GEO_FLY ? 2 * 3 * N3 + S::FLY_OUT : 0);
+  int* eo = reinterpret_cast<int*>(lay + SL) - 2;  // two ints at the end of the slice
+  int* en = eo + 1;
+  const PhysT<T> ph = make_phys<T>(kp);
+  if (grp.rank() == 0) {
+    int c[3];
+    if (s == 1) {
+      c[0] = i % kp.nc[0];
+      c[1] = (i / kp.nc[0]) % kp.nc[1];
+      c[2] = i / (kp.nc[0] * kp.nc[1]);
+    } else {
+      c[d] = 0;
+      c[t1] = i % kp.nc[t1];
+      c[t2] = i / kp.nc[t1];
+    }
+    const int e = c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+    c[d] += s ? 1 : -1;
+    int wl = 0;
+    if (c[d] < 0 || c[d] >= kp.nc[d]) {
+      if (kp.periodic[d])
+        c[d] = (c[d] + kp.nc[d]) % kp.nc[d];
+      else
+        wl = 1;
+    }
+    const int n = wl ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+    eo[0] = e;
+    en[0] = n;
+    const double te = kp.tau[e];
+    tau_f[0] = T(wl ? te : fmax(te, kp.tau[n]));
+  }
+  grp.sync();
+  const T* Ud = static_cast<const T*>(kp.Udev);
+  if (GEO == GEO_FLY) {
+    const T* X = static_cast<const T*>(kp.xyzT);
+    for (int r = grp.rank(); r < 3 * N3; r += 32) {
+      sx[r] = X[(size_t)eo[0] * 3 * N3 + r];
+      sxn[r] = X[(size_t)(en[0] >= 0 ? en[0] : eo[0]) * 3 * N3 + r];
+    }
+    grp.sync();
+  }
+  if (d == 0)
+    face_pair_terms<T, N, QC, QV, 1, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+  else if (d == 1)
+    face_pair_terms<T, N, QC, QV, 1, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+  else
+    face_pair_terms<T, N, QC, QV, 1, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+}
+
 template <typename T, int N, int QC, int QV, int GEO>
 int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) {
-  constexpr int CB = faces_per_cta<T, N, QC, QV, GEO>();
-  constexpr size_t smem = face_smem_bytes<T, N, QC, QV, CB, GEO>();
-  static_assert(smem <= 227 * 1024, "face kernel shared memory");
-  auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
-  int extra = 0;
+  int extra_items = 0;
   for (int d = 0; d < 3; ++d) {
     if (kp.periodic[d]) continue;
     const int plane = kp.nc[d == 0 ? 1 : 0] * kp.nc[d == 2 ? 1 : 2];
-    const int nbk = (plane + CB - 1) / CB;
-    if (nbk > extra) extra = nbk;
+    if (plane > extra_items) extra_items = plane;
   }
-  const dim3 grid((kp.Nc + CB - 1) / CB + extra, 3);
-  k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
+  if constexpr (sizeof(T) == 4) {
+    constexpr int WPC = 8;
+    constexpr size_t smem = face_warp_smem_bytes<T, N, QC, QV, WPC, GEO>();
+    static_assert(smem <= 227 * 1024, "face kernel shared memory");
+    auto k = dg_face_warp_kernel<T, N, QC, QV, WPC, GEO>;
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+      attr = true;
+    }
+    const dim3 grid((kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
+    k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<T*>(FB));
+  } else {
+    constexpr int CB = faces_per_cta<T, N, QC, QV, GEO>();
+    constexpr size_t smem = face_smem_bytes<T, N, QC, QV, CB, GEO>();
+    static_assert(smem <= 227 * 1024, "face kernel shared memory");
+    auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+      attr = true;
+    }
+    const dim3 grid((kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
+    k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
