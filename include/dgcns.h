@@ -203,6 +203,11 @@ int dg_cns_diagnostics_noalloc(dgcns_ctx* ctx, const double* U, const void* L_of
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int dg_cns_launch_count(const dgcns_ctx* ctx, int64_t* count);
 
+/* Synchronizes the context's stream and reports whether any kernel of this context gave up a
+   bounded wait (its pipelined copies did not land within the poll limit) since the last call:
+   DGCNS_ERR_TIMEOUT then (the affected results are invalid), else DGCNS_OK.  The flag is cleared. */
+int dg_cns_status(dgcns_ctx* ctx);
+
 /* Kernel kinds of the per-kernel timing. */
 #define DGCNS_KT_CELL 0        /* cell integrals alone (split organisation; residual of the face-centric one) */
 #define DGCNS_KT_FACE 1        /* element-centric face integrals alone (split organisation) */

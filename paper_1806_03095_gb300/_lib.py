@@ -24,7 +24,7 @@ NOALLOC_SCRATCH_BYTES = 16 << 20  # static device scratch of dg_cns_diagnostics_
 EXPORTS = ("dg_cns_create", "dg_cns_destroy", "dg_cns_set_stream", "dg_cns_sizes", "dg_cns_node_coords",
            "dg_cns_apply", "dg_cns_inverse_mass", "dg_cns_rk_stage", "dg_cns_rk_steps", "dg_cns_diagnostics",
            "dg_cns_diagnostics_noalloc", "dg_cns_adjoint_apply", "dg_cns_rk_stage_adjoint",
-           "dg_cns_kinetic_energy_gradient", "dg_cns_launch_count", "dg_cns_timing", "dg_cns_kernel_times",
+           "dg_cns_kinetic_energy_gradient", "dg_cns_launch_count", "dg_cns_status", "dg_cns_timing", "dg_cns_kernel_times",
            "dg_cns_last_error")
 
 # Kernel kinds of dg_cns_kernel_times (DGCNS_KT_*).
@@ -76,6 +76,7 @@ def load(path=LIB_PATH):
         "dg_cns_rk_stage_adjoint": ([vp, ci, cd, vp, vp, vp], ci),
         "dg_cns_kinetic_energy_gradient": ([vp, vp, vp], ci),
         "dg_cns_launch_count": ([vp, i64p], ci),
+        "dg_cns_status": ([vp], ci),
         "dg_cns_timing": ([vp, ci], ci),
         "dg_cns_kernel_times": ([vp, dp, i64p, ci], ci),
         "dg_cns_last_error": ([vp], ctypes.c_char_p),

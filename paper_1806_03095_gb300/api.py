@@ -178,6 +178,12 @@ class DGCNS:
         self._check(self.lib.dg_cns_launch_count(self.ctx, ctypes.byref(c)))
         return c.value
 
+    def dg_cns_status(self):
+        """Raise DGCNSError(TIMEOUT) if a kernel of this context gave up a bounded wait."""
+        self._check(self.lib.dg_cns_status(self.ctx))
+
+    status = dg_cns_status
+
     def dg_cns_timing(self, enable):
         """Start (clearing the totals) or stop per-kernel CUDA-event timing on the context's stream."""
         self._check(self.lib.dg_cns_timing(self.ctx, 1 if enable else 0))

@@ -967,14 +967,16 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
 // ---------------------------------------------------------------------------
 template <typename T, int N, int CB, int GEO, class G = CtaGroup>
 __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const KParams& kp, int e0, int nb,
-                             bool negate, bool add_force, G grp = G(), const T* sx = nullptr, T* go = nullptr) {
+                             bool negate, bool add_force, G grp = G(), const T* sx = nullptr, T* go = nullptr,
+                             const T* sin = nullptr) {
+  // sin: optional separate input (default: sr, overwritten by the result)
   if (GEO == GEO_FLY) fill_mass_geo<T, N, CB>(sx, ma, tb.eSm, tb.eDm, go, nb, grp);
   constexpr int N3 = N * N * N;
   const int nbl = nb * 5;
   T* A = ma;
   T* B = ma + CB * 5 * N3;
   const T detJ = kconst<T>(kp).detJ;
-  sweep<T, 0, N, N, N, N, 1, false>(sr, A, tb.eSmiT, nbl, grp);
+  sweep<T, 0, N, N, N, N, 1, false>(sin ? sin : sr, A, tb.eSmiT, nbl, grp);
   grp.sync();
   sweep<T, 1, N, N, N, N, 1, false>(A, B, tb.eSmiT, nbl, grp);
   grp.sync();

@@ -7,6 +7,7 @@
 #include "dg_adjoint_faces.cuh"
 #include "dg_faces.cuh"
 #include "dg_kernels.cuh"
+#include "dg_mass.cuh"
 #include "dg_launchers.h"
 
 namespace dgcns {
@@ -845,11 +846,22 @@ template <typename T, int N, int QC, int QV, int GEO>
 int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU,
                     double* Uout, cudaStream_t st) {
   // FP32: warp per cell (latency-bound otherwise); FP64: CTA per cell batch (FP64-pipe bound)
-  constexpr bool WARP = sizeof(T) == 4 && warp_smem_bytes<T, N, QC, QV, 4, true, true, true, GEO>() <= 227 * 1024;
+  // (only while a warp's slice stays small: at k = 5 a cell needs ~49 KB, which would leave 4 warps per SM)
+  constexpr bool WARP =
+      sizeof(T) == 4 && warp_slice_elems<T, N, QC, QV, true, true, true, GEO>() * sizeof(T) <= 20 * 1024;
   switch (mode) {
     case OP_CELL: return launch_op_any<T, N, QC, QV, GEO, WARP, true, false, false>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_FACE: return launch_op_any<T, N, QC, QV, GEO, WARP, false, true, false>(kp, U, Rin, Rout, dU, Uout, st);
-    case OP_MASS: return launch_op_any<T, N, QC, QV, GEO, WARP, false, false, true>(kp, U, Rin, Rout, dU, Uout, st);
+    case OP_MASS:
+      if constexpr (mass_tma_ok<T, N>() && GEO != GEO_FLY) {
+        // the TMA-pipelined kernel needs 16-byte aligned arrays and no body force (no state read)
+        const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+        if (!kp.has_bf && kp.err != nullptr && al(Rin) && al(Rout) && al(dU) && al(U) && al(Uout)) {
+          if (kp.out_mode == 2) return launch_mass_tma<T, N, QC, QV, true, GEO>(kp, Rin, Rout, dU, U, Uout, st);
+          return launch_mass_tma<T, N, QC, QV, false, GEO>(kp, Rin, Rout, dU, U, Uout, st);
+        }
+      }
+      return launch_op_any<T, N, QC, QV, GEO, WARP, false, false, true>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_FACE:
       return launch_op_any<T, N, QC, QV, GEO, WARP, true, true, false>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_MASS:

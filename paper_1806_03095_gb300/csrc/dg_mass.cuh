@@ -1,0 +1,185 @@
+// Inverse mass (Sec. 2.3) and, optionally, the 2N stage update as a persistent, TMA-pipelined kernel.
+// The standalone M^{-1} (and the split organisation's M^{-1} + update) has little arithmetic per byte
+// in FP32, so it is bound by how many bytes each SM keeps in flight: every CTA streams batches of CB
+// consecutive cells (one contiguous range) into shared memory with cp.async.bulk, double-buffered on
+// two mbarriers, so that the copy of batch i+1 overlaps the sweeps of batch i.  Waits are bounded:
+// after kWaitPolls unsuccessful polls the kernel sets the context's error word and returns.
+#pragma once
+#include <cstdint>
+
+#include "dg_kernels.cuh"
+
+namespace dgcns {
+
+constexpr long long kWaitPolls = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completion on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Poll the phase with the given parity; false after kWaitPolls unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitPolls; ++i) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Usable when every cell's block is a multiple of 16 bytes in the residual type and in FP64.
+template <typename T, int N>
+constexpr bool mass_tma_ok() {
+  return (5 * N * N * N * sizeof(T)) % 16 == 0 && (5 * N * N * N * 8) % 16 == 0;
+}
+
+template <typename T, int N, int QC, int QV, bool STAGE>
+constexpr int mass_tma_table_elems() {
+  return (int)(((table_elems<N, QC, QV>() * sizeof(T) + 15) / 16) * 16 / sizeof(T));
+}
+
+template <typename T, int N, int QC, int QV, bool STAGE>
+constexpr size_t mass_tma_bytes(int cb) {
+  const size_t BV = (size_t)cb * 5 * N * N * N;
+  return 16 + (STAGE ? 2 * BV * 8 : 0) + mass_tma_table_elems<T, N, QC, QV, STAGE>() * sizeof(T) +
+         (2 * BV + (STAGE ? 2 * BV : 0) + BV + 2 * BV) * sizeof(T);
+}
+
+// Cells per batch: the largest CB <= 8 with the CTA's shared memory below ~56 KB (4 CTAs per SM).
+template <typename T, int N, int QC, int QV, bool STAGE>
+constexpr int mass_tma_cells() {
+  int cb = 8;
+  while (cb > 1 && mass_tma_bytes<T, N, QC, QV, STAGE>(cb) > 56 * 1024) --cb;
+  return cb;
+}
+
+constexpr int kMassThreads = 256;
+
+// out_mode 0/1: Rout = (-1 if out_mode 1) M^{-1} Rin;  STAGE (out_mode 2): dU <- A dU + dt (-M^{-1} Rin),
+// U_out <- U + B dU.  Rin may alias Rout, U may alias U_out (each batch is read before it is written).
+template <typename T, int N, int QC, int QV, int CB, bool STAGE, int GEO>
+__global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams kp, const double* U, const T* Rin,
+                                                                   T* Rout, T* dU, double* Uout) {
+  constexpr int N3 = N * N * N, CV = 5 * N3, BV = CB * CV;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  double* bufU = reinterpret_cast<double*>(smem_raw + 16);  // STAGE: [2][BV]
+  T* stab = reinterpret_cast<T*>(smem_raw + 16 + (STAGE ? 2 * BV * 8 : 0));
+  T* bufR = stab + mass_tma_table_elems<T, N, QC, QV, STAGE>();  // [2][BV]
+  T* bufD = bufR + 2 * BV;                                        // STAGE: [2][BV]
+  T* sr = bufD + (STAGE ? 2 * BV : 0);                            // result [BV]
+  T* ma = sr + BV;                                                // sweep arena [2 BV]
+  const int nbatch = (kp.Nc + CB - 1) / CB;
+  if ((int)blockIdx.x >= nbatch) return;
+  const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
+  const bool readD = STAGE && kp.A != 0.0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int b, int slot) {  // thread 0
+    const int e0 = b * CB, nb = min(CB, kp.Nc - e0);
+    const uint32_t bt = (uint32_t)(nb * CV * sizeof(T)), b8 = (uint32_t)(nb * CV * 8);
+    mbar_expect_tx(&bar[slot], bt + (STAGE ? b8 + (readD ? bt : 0u) : 0u));
+    bulk_load(bufR + slot * BV, Rin + (size_t)e0 * CV, bt, &bar[slot]);
+    if (STAGE) {
+      bulk_load(bufU + slot * BV, U + (size_t)e0 * CV, b8, &bar[slot]);
+      if (readD) bulk_load(bufD + slot * BV, dU + (size_t)e0 * CV, bt, &bar[slot]);
+    }
+  };
+  if (threadIdx.x == 0) issue(blockIdx.x, 0);
+  int it = 0;
+  bool timed_out = false;
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+    const int slot = it & 1;
+    const int bn = b + gridDim.x;
+    if (threadIdx.x == 0 && bn < nbatch) issue(bn, slot ^ 1);  // slot^1 was released at the end of it-1
+    const int e0 = b * CB, nb = min(CB, kp.Nc - e0);
+    const bool ok = mbar_wait(&bar[slot], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    inverse_mass<T, N, CB, GEO>(nullptr, sr, ma, tb, kp, e0, nb, kp.out_mode != 0, false, CtaGroup(), nullptr,
+                                nullptr, bufR + slot * BV);
+    const size_t base = (size_t)e0 * CV;
+    if (STAGE) {
+      const T A = T(kp.A), dt = T(kp.dt);
+      const double B = kp.B;
+      const T* dold = bufD + slot * BV;
+      const double* uold = bufU + slot * BV;
+      for (int i = threadIdx.x; i < nb * CV; i += blockDim.x) {
+        const T du = (readD ? A * dold[i] : T(0)) + dt * sr[i];
+        dU[base + i] = du;
+        Uout[base + i] = uold[i] + B * double(du);
+      }
+    } else {
+      for (int i = threadIdx.x; i < nb * CV; i += blockDim.x) Rout[base + i] = sr[i];
+    }
+    __syncthreads();
+  }
+  if (timed_out) {
+    // give the copies still in flight a bounded chance to land before the CTA exits
+    if (threadIdx.x == 0) {
+      atomicExch(kp.err, 1);
+      mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1));
+      mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N, int QC, int QV, bool STAGE, int GEO>
+int launch_mass_tma(const KParams& kp, const void* Rin, void* Rout, void* dU, const double* U, double* Uout,
+                    cudaStream_t st) {
+  constexpr int CB = mass_tma_cells<T, N, QC, QV, STAGE>();
+  constexpr size_t smem = mass_tma_bytes<T, N, QC, QV, STAGE>(CB);
+  static_assert(smem <= 227 * 1024, "mass kernel shared memory");
+  auto k = dg_mass_tma_kernel<T, N, QC, QV, CB, STAGE, GEO>;
+  static int grid_per_sm = 0;
+  static int nsm = 0;
+  if (grid_per_sm == 0) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, k, kMassThreads, smem) != cudaSuccess ||
+        grid_per_sm < 1)
+      return -1;
+  }
+  const int nbatch = (kp.Nc + CB - 1) / CB;
+  const int grid = nbatch < nsm * grid_per_sm ? nbatch : nsm * grid_per_sm;
+  k<<<grid, kMassThreads, smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout), static_cast<T*>(dU),
+                                      Uout);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace dgcns

@@ -266,6 +266,7 @@ struct dgcns_ctx {
   float* g32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the mixed form
   size_t gsize[5] = {0, 0, 0, 0, 0};
   double* d_partial = nullptr;
+  int* d_err = nullptr;  // error word of the kernels with bounded waits
   int diag_blocks = 0;
   int64_t launches = 0;
   // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
@@ -590,11 +591,18 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   int nblk = 0;
   c->L.diag_fp64(kd, nullptr, nullptr, nullptr, &nblk, c->stream);
   c->diag_blocks = nblk;
-  if (cudaMalloc(&c->d_partial, ((size_t)nblk + 1) * 10 * sizeof(double)) != cudaSuccess) {
+  if (cudaMalloc(&c->d_partial, ((size_t)nblk + 1) * 10 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     dg_cns_destroy(c);
     return DGCNS_ERR_OOM;
   }
+  if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    dg_cns_destroy(c);
+    return DGCNS_ERR_CUDA;
+  }
+  c->kp.err = c->d_err;
   if (cudaGetLastError() != cudaSuccess) {
     dg_cns_destroy(c);
     return DGCNS_ERR_CUDA;
@@ -619,6 +627,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFree(c->d_partial);
+  cudaFree(c->d_err);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
     cudaFree(c->g32[i]);
@@ -1037,6 +1046,19 @@ int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, do
 int dg_cns_launch_count(const dgcns_ctx* c, int64_t* count) {
   if (!c || !count) return DGCNS_ERR_INVALID_ARG;
   *count = c->launches;
+  return DGCNS_OK;
+}
+
+int dg_cns_status(dgcns_ctx* c) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  int h = 0;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(c, "status read");
+  if (h) {
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(c, "status reset");
+    return fail(c, DGCNS_ERR_TIMEOUT, "a bounded wait in a kernel gave up (its results are invalid)");
+  }
   return DGCNS_OK;
 }
 

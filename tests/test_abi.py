@@ -78,6 +78,7 @@ def test_null_context_calls_fail_cleanly(lib):
     c = ctypes.c_int64()
     assert lib.dg_cns_launch_count(None, ctypes.byref(c)) == -1
     assert lib.dg_cns_timing(None, 1) == -1
+    assert lib.dg_cns_status(None) == -1
     assert lib.dg_cns_kernel_times(None, None, None, 0) == -1
 
 

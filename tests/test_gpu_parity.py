@@ -149,6 +149,37 @@ def test_inverse_mass_fp64(k):
     assert l2 < TOL64 and mx < TOL64
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_inverse_mass_many_batches(precision):
+    """7581 cells: the pipelined inverse-mass kernel runs several batches per CTA, with a ragged last batch."""
+    g, op = pair((21, 19, 19), 3, precision=precision)
+    R = inputs.uniform((op.mesh.Nc, 5, op.mesh.n ** 3), 19)
+    out = g.inverse_mass(on_gpu(R).to(g.rdtype))
+    ref = op.mass_solve(R)
+    l2, mx = rel_err(out.double(), ref)
+    tol = TOL64 if precision == 0 else 1e-5
+    assert l2 < tol and mx < 10 * tol, (l2, mx)
+    g.status()
+
+
+@pytest.mark.parametrize("stage", [0, 3])
+def test_split_rk_stage_many_batches_sampled(stage):
+    """Split organisation on 1716 cells (the pipelined M^-1 + update kernel runs several batches per CTA),
+    checked on 24 sampled cells whose L the oracle evaluates one by one."""
+    g, op = pair((13, 12, 11), 3, kernel=0)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 20)
+    dU = inputs.uniform(U.shape, 21)
+    dt = 1e-3
+    Ug, dUg, Uo = on_gpu(U), on_gpu(dU), g.empty_state()
+    g.rk_stage(stage, dt, 0.0, Ug, dUg, Uo)
+    g.status()
+    E = torch.as_tensor(sorted(set(int(v) for v in torch.linspace(0, op.mesh.Nc - 1, 24).round().long())))
+    dU_ref = ork.A[stage] * dU[E] + dt * op.L_cells(U, E)
+    U_ref = U[E] + ork.B[stage] * dU_ref
+    assert max(rel_err(dUg.cpu()[E], dU_ref)) < TOL64
+    assert max(rel_err(Uo.cpu()[E], U_ref)) < TOL64
+
+
 @pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_L_with_body_force_and_walls(kernel):
     g, op = pair((2, 2, 2), 3, periodic=(1, 0, 1), lo=(0, -1, 0), hi=(2 * PI, 1, PI), Re=180.0, u_mach=18.3,
