@@ -448,7 +448,8 @@ def memory_bound_kernels(reps=20):
 
 def k_sweep(steps=2):
     """Throughput against the polynomial degree (the paper's throughput-versus-k study, Sec. 3): TGV meshes of
-    about 84M DoFs for k = 2..6 (FP64) and k = 3..5 (mixed), fused and face-centric kernels."""
+    about 84M DoFs for k = 2..6 (FP64) and k = 3..5 (mixed), fused and face-centric kernels, and (k = 2..5, FP64,
+    face-centric) with the paper's own quadrature, the 3/2 rule on both terms."""
     from paper_1806_03095_gb300 import configs
     device = torch.cuda.current_device()
     out = {}
@@ -463,6 +464,16 @@ def k_sweep(steps=2):
                 out[key] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps), "unit": UNIT}
                 del ctx, bufs
                 torch.cuda.empty_cache()
+        if k <= 5:
+            # the paper's own quadrature: the 3/2 rule on the viscous term too
+            cfg = dict(configs.tgv(n, k, precision=0, kernel=2))
+            cfg["nq_visc"] = cfg["nq_conv"]
+            ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+            nodes = bufs[0].numel() // 5
+            out["k%d_fp64_faces_3/2_rule_both_terms" % k] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps),
+                                                              "unit": UNIT, "nq": [cfg["nq_conv"], cfg["nq_visc"]]}
+            del ctx, bufs
+            torch.cuda.empty_cache()
     return out
 
 

@@ -92,13 +92,16 @@ def test_residual_terms_fp64(what, op_code, kernel):
     assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
-@pytest.mark.parametrize("qc,qv", [(4, 4), (5, 5)])
-def test_other_quadrature_rules(qc, qv):
-    """Standard rule (k+1 for both terms) and the paper's 3/2-rule on both terms (Sec. 2.2.3)."""
-    g, op = pair((2, 2, 2), 3, qc, qv)
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("k,qc,qv", [(3, 4, 4), (3, 5, 5), (5, 6, 6), (2, 4, 4), (4, 7, 7), (5, 8, 8)])
+def test_other_quadrature_rules(k, qc, qv, kernel):
+    """The k+1 rule on both terms, and the paper's 3/2 rule on both terms (Sec. 2.2.3)."""
+    g, op = pair((2, 2, 2), k, qc, qv, kernel=kernel)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 8)
     l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
-    assert l2 < TOL64 and mx < TOL64
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
