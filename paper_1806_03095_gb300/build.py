@@ -46,14 +46,14 @@ def parts():
     return int(re.search(r"#define DGCNS_PARTS (\d+)", text).group(1))
 
 
-def _sources_digest():
+def _sources_digest(extra=()):
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for name in sorted(os.listdir(d)):
             if name.endswith((".cu", ".cuh", ".h")):
                 h.update(name.encode())
                 h.update(open(os.path.join(d, name), "rb").read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + list(extra)).encode())
     return h.hexdigest()
 
 
@@ -66,7 +66,7 @@ def _run(cmd):
 
 def build(jobs=None, force=False, verbose=False, extra=()):
     """Compile libdgcns.so if the sources changed; returns the library path."""
-    digest = _sources_digest()
+    digest = _sources_digest(extra)
     stamp = os.path.join(BUILD, "stamp")
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
         return LIB

@@ -40,6 +40,28 @@ struct WarpGroup {
   __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
+// Elementwise pass over i = rank, rank + stride, ... < n (at most PER indices per thread): a thread
+// issues its loads (in chunks of 8) before the matching stores, so that their latencies overlap
+// instead of adding up.
+template <int PER, class Ld, class St>
+__device__ __forceinline__ void batched_pass(int rank, int stride, int n, Ld ld, St st) {
+  constexpr int CH = PER < 8 ? PER : 8;
+#pragma unroll 1
+  for (int j0 = 0; j0 < PER; j0 += CH) {
+    decltype(ld(0)) v[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int i = (j0 + j) * stride + rank;
+      if (j0 + j < PER && i < n) v[j] = ld(i);
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int i = (j0 + j) * stride + rank;
+      if (j0 + j < PER && i < n) st(i, v[j]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory tables
 // ---------------------------------------------------------------------------

@@ -13,7 +13,16 @@
 namespace dgcns {
 
 
-// Cells per CTA: the largest batch (<= 4 for FP32, <= 8 for FP64) whose shared
+// Batch caps of the CTA-wide kernels (compile-time tuning parameters: cells per CTA of the FP64
+// operator kernel, faces per CTA of the FP64 face kernel).
+#ifndef DGCNS_FP64_CELL_CAP
+#define DGCNS_FP64_CELL_CAP 8
+#endif
+#ifndef DGCNS_FP64_FACE_CAP
+#define DGCNS_FP64_FACE_CAP 8
+#endif
+
+// Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
 // memory stays below ~112 KB, so that two or more CTAs fit on one SM (228 KB).
 template <typename T, int N, int QC, int QV>
 constexpr int cells_per_cta() {
@@ -21,7 +30,7 @@ constexpr int cells_per_cta() {
   constexpr int arena = S::CELL_ARENA > S::FACE_ARENA ? S::CELL_ARENA : S::FACE_ARENA;
   constexpr int per_cell = (3 * 5 * S::N3 + arena) * (int)sizeof(T) + 8;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_cell;
-  constexpr int cap = sizeof(T) == 4 ? 4 : 8;
+  constexpr int cap = sizeof(T) == 4 ? 4 : DGCNS_FP64_CELL_CAP;
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
@@ -68,6 +77,27 @@ constexpr size_t op_smem_bytes() {
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
 }
 
+// 2N update of a batch: dU <- A dU + dt L (residual type), U_out <- U + B dU (FP64); the loads of U and
+// dU of a thread are issued together before the stores.
+template <int PER, typename T>
+__device__ __forceinline__ void stage_update(const KParams& kp, const double* U, T* dU, double* Uout, const T* sr,
+                                             size_t base, int nvals, int rank, int stride) {
+  struct UD {
+    double u;
+    T d;
+  };
+  const T A = T(kp.A), dt = T(kp.dt);
+  const double B = kp.B;
+  const bool readD = kp.A != 0.0;
+  batched_pass<PER>(rank, stride, nvals,
+                    [&](int i) { return UD{U[base + i], readD ? dU[base + i] : T(0)}; },
+                    [&](int i, UD v) {
+                      const T du = A * v.d + dt * sr[i];
+                      dU[base + i] = du;
+                      Uout[base + i] = v.u + B * double(du);
+                    });
+}
+
 // component c of the reference state U_ref = (rho_r, 0, 0, 0, rho_r c_v T_0)
 __device__ __forceinline__ double ref_of(const KParams& kp, int c) {
   return c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0);
@@ -106,11 +136,22 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
 
   const size_t base = (size_t)e0 * 5 * N3;
   const int nvals = nb * 5 * N3;
+  constexpr int PER = (CB * 5 * N3 + op_threads<T>() - 1) / op_threads<T>();  // values per thread
   const bool need_u = CELL || FACE || (MASS && kp.has_bf);
   const T* Ud = static_cast<const T*>(kp.Udev);
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
-    sr[i] = CELL ? T(0) : Rin[base + i];
+  if (need_u) {
+    if (Ud)
+      batched_pass<PER>(threadIdx.x, blockDim.x, nvals, [&](int i) { return Ud[base + i]; },
+                        [&](int i, T v) { su[i] = v; });
+    else
+      batched_pass<PER>(threadIdx.x, blockDim.x, nvals, [&](int i) { return U[base + i]; },
+                        [&](int i, double v) { su[i] = T(v - ref_of(kp, (i / N3) % 5)); });
+  }
+  if (CELL) {
+    for (int i = threadIdx.x; i < nvals; i += blockDim.x) sr[i] = T(0);
+  } else {
+    batched_pass<PER>(threadIdx.x, blockDim.x, nvals, [&](int i) { return Rin[base + i]; },
+                      [&](int i, T v) { sr[i] = v; });
   }
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT) + (size_t)e0 * 3 * N3;
@@ -125,7 +166,9 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
     const T* F = static_cast<const T*>(kp.fbuf) + (size_t)e0 * fbuf_per_cell<N>();
     __syncthreads();
     if constexpr (S::CELL_ARENA >= fbuf_per_cell<N>()) {
-      for (int i = threadIdx.x; i < nb * fbuf_per_cell<N>(); i += blockDim.x) ar[i] = F[i];
+      constexpr int PF = (CB * fbuf_per_cell<N>() + op_threads<T>() - 1) / op_threads<T>();
+      batched_pass<PF>(threadIdx.x, blockDim.x, nb * fbuf_per_cell<N>(), [&](int i) { return F[i]; },
+                       [&](int i, T v) { ar[i] = v; });
       __syncthreads();
       gather_face_shares<T, N>(sr, ar, tb, nb, CtaGroup());
     } else {
@@ -186,13 +229,7 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
 
   if (kp.out_mode == 2) {
     // 2N update: dU in the residual type, the state accumulated in FP64
-    const T A = T(kp.A), dt = T(kp.dt);
-    const double B = kp.B;
-    for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-      const T du = (kp.A != 0.0 ? A * dU[base + i] : T(0)) + dt * sr[i];
-      dU[base + i] = du;
-      Uout[base + i] = U[base + i] + B * double(du);
-    }
+    stage_update<PER>(kp, U, dU, Uout, sr, base, nvals, threadIdx.x, blockDim.x);
   } else {
     for (int i = threadIdx.x; i < nvals; i += blockDim.x) Rout[base + i] = sr[i];
   }
@@ -732,11 +769,20 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
   const PhysT<T> ph = make_phys<T>(kp);
   const size_t base = (size_t)e0 * 5 * N3;
   constexpr int nvals = 5 * N3;
+  constexpr int PER = (nvals + 31) / 32;  // values per lane
   const bool need_u = CELL || FACE || (MASS && kp.has_bf);
   const T* Ud = static_cast<const T*>(kp.Udev);
-  for (int i = grp.rank(); i < nvals; i += 32) {
-    if (need_u) su[i] = Ud ? Ud[base + i] : T(U[base + i] - ref_of(kp, (i / N3) % 5));
-    sr[i] = CELL ? T(0) : Rin[base + i];
+  if (need_u) {
+    if (Ud)
+      batched_pass<PER>(grp.rank(), 32, nvals, [&](int i) { return Ud[base + i]; }, [&](int i, T v) { su[i] = v; });
+    else
+      batched_pass<PER>(grp.rank(), 32, nvals, [&](int i) { return U[base + i]; },
+                        [&](int i, double v) { su[i] = T(v - ref_of(kp, (i / N3) % 5)); });
+  }
+  if (CELL) {
+    for (int i = grp.rank(); i < nvals; i += 32) sr[i] = T(0);
+  } else {
+    batched_pass<PER>(grp.rank(), 32, nvals, [&](int i) { return Rin[base + i]; }, [&](int i, T v) { sr[i] = v; });
   }
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT) + (size_t)e0 * 3 * N3;
@@ -748,7 +794,8 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
     const T* F = static_cast<const T*>(kp.fbuf) + (size_t)e0 * fbuf_per_cell<N>();
     grp.sync();
     if constexpr (S::CELL_ARENA >= fbuf_per_cell<N>()) {
-      for (int i = grp.rank(); i < fbuf_per_cell<N>(); i += 32) ar[i] = F[i];
+      batched_pass<(fbuf_per_cell<N>() + 31) / 32>(grp.rank(), 32, fbuf_per_cell<N>(), [&](int i) { return F[i]; },
+                                                   [&](int i, T v) { ar[i] = v; });
       grp.sync();
       gather_face_shares<T, N>(sr, ar, tb, 1, grp);
     } else {
@@ -801,13 +848,7 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
     inverse_mass<T, N, 1, GEO>(su, sr, ar, tb, kp, e0, 1, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0, grp,
                                sx, go);
   if (kp.out_mode == 2) {
-    const T A = T(kp.A), dt = T(kp.dt);
-    const double B = kp.B;
-    for (int i = grp.rank(); i < nvals; i += 32) {
-      const T du = (kp.A != 0.0 ? A * dU[base + i] : T(0)) + dt * sr[i];
-      dU[base + i] = du;
-      Uout[base + i] = U[base + i] + B * double(du);
-    }
+    stage_update<PER>(kp, U, dU, Uout, sr, base, nvals, grp.rank(), 32);
   } else {
     for (int i = grp.rank(); i < nvals; i += 32) Rout[base + i] = sr[i];
   }
@@ -964,7 +1005,8 @@ constexpr int faces_per_cta() {
   constexpr int geo = GEO == GEO_FLY ? 2 * 3 * S::N3 + S::FLY_OUT : 0;
   constexpr int per_face = (PairSizes<N, QC, QV>::LAYERS + 5 * S::N2 + arena + geo) * (int)sizeof(T) + 16;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_face;
-  return cb < 1 ? 1 : (cb > 8 ? 8 : cb);
+  constexpr int cap = sizeof(T) == 4 ? 8 : DGCNS_FP64_FACE_CAP;
+  return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
 template <typename T, int N, int QC, int QV, int CB, int GEO>
