@@ -144,14 +144,10 @@ class ClockSampler:
 
 # -- native arm --------------------------------------------------------------------------------------
 def run_stages(ctx, nsteps, dt, t0, bufs):
-    """nsteps RK(5,4) steps by ping-pong of (U, U_tmp); returns the buffer holding the state."""
+    """nsteps RK(5,4) steps through dg_cns_rk_steps (ping-pong of U and U_tmp inside the library, the state
+    back in U at the end); returns U."""
     U, Ut, dU = bufs
-    a, b = U, Ut
-    for n in range(nsteps):
-        for s in range(5):
-            ctx.rk_stage(s, dt, t0 + n * dt, a, dU, b)
-            a, b = b, a
-    return a
+    return ctx.rk_steps(nsteps, dt, t0, U, Ut, dU)
 
 
 def time_native(cfg, steps, warmup, device, kernel_times=None):

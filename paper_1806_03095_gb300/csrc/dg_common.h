@@ -88,6 +88,8 @@ struct KParams {
   // Face shares [Nc][6][2][5][N^2] written by the face-centric face kernel; when set, the cell kernel
   // (without FACE) adds them to the residual.
   const void* fbuf;
+  // Optional output (mixed form, stage update): float(U_out - U_ref), the next stage's deviation state.
+  void* devOut;
   // Device error word of the context: kernels with bounded waits set it to 1 when a wait gives up.
   int* err;
   KConst<double> cd;

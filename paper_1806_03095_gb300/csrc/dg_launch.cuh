@@ -14,7 +14,7 @@ namespace dgcns {
 
 
 // Batch caps of the CTA-wide kernels (compile-time tuning parameters: cells per CTA of the FP64
-// operator kernel, faces per CTA of the FP64 face kernel).
+// operator kernel, faces per CTA of the FP64 face kernel; 4 faces per CTA were 3 % slower than 8).
 #ifndef DGCNS_FP64_CELL_CAP
 #define DGCNS_FP64_CELL_CAP 8
 #endif
@@ -30,7 +30,9 @@ constexpr int cells_per_cta() {
   constexpr int arena = S::CELL_ARENA > S::FACE_ARENA ? S::CELL_ARENA : S::FACE_ARENA;
   constexpr int per_cell = (3 * 5 * S::N3 + arena) * (int)sizeof(T) + 8;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_cell;
-  constexpr int cap = sizeof(T) == 4 ? 4 : DGCNS_FP64_CELL_CAP;
+  // FP64 at k >= 3: 2 cells per CTA (4 CTAs per SM hide more latency than 4 cells in 2 CTAs: the face-
+  // centric cell + stage kernel at k = 3 is 2.5 % faster, measured)
+  constexpr int cap = sizeof(T) == 4 ? 4 : (N >= 4 && DGCNS_FP64_CELL_CAP > 2 ? 2 : DGCNS_FP64_CELL_CAP);
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
@@ -78,8 +80,9 @@ constexpr size_t op_smem_bytes() {
 }
 
 // 2N update of a batch: dU <- A dU + dt L (residual type), U_out <- U + B dU (FP64); the loads of U and
-// dU of a thread are issued together before the stores.
-template <int PER, typename T>
+// dU of a thread are issued together before the stores.  With kp.devOut (mixed form inside a
+// multi-step call) also float(U_out - U_ref), the deviation state the next stage reads.
+template <int PER, int N3, typename T>
 __device__ __forceinline__ void stage_update(const KParams& kp, const double* U, T* dU, double* Uout, const T* sr,
                                              size_t base, int nvals, int rank, int stride) {
   struct UD {
@@ -89,12 +92,18 @@ __device__ __forceinline__ void stage_update(const KParams& kp, const double* U,
   const T A = T(kp.A), dt = T(kp.dt);
   const double B = kp.B;
   const bool readD = kp.A != 0.0;
+  T* dev = static_cast<T*>(kp.devOut);
   batched_pass<PER>(rank, stride, nvals,
                     [&](int i) { return UD{U[base + i], readD ? dU[base + i] : T(0)}; },
                     [&](int i, UD v) {
                       const T du = A * v.d + dt * sr[i];
                       dU[base + i] = du;
-                      Uout[base + i] = v.u + B * double(du);
+                      const double uo = v.u + B * double(du);
+                      Uout[base + i] = uo;
+                      if (dev) {
+                        const int c = (i / N3) % 5;
+                        dev[base + i] = T(uo - (c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0)));
+                      }
                     });
 }
 
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
 
   if (kp.out_mode == 2) {
     // 2N update: dU in the residual type, the state accumulated in FP64
-    stage_update<PER>(kp, U, dU, Uout, sr, base, nvals, threadIdx.x, blockDim.x);
+    stage_update<PER, N3>(kp, U, dU, Uout, sr, base, nvals, threadIdx.x, blockDim.x);
   } else {
     for (int i = threadIdx.x; i < nvals; i += blockDim.x) Rout[base + i] = sr[i];
   }
@@ -848,7 +857,7 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
     inverse_mass<T, N, 1, GEO>(su, sr, ar, tb, kp, e0, 1, CELL || FACE || kp.out_mode != 0, kp.has_bf != 0, grp,
                                sx, go);
   if (kp.out_mode == 2) {
-    stage_update<PER>(kp, U, dU, Uout, sr, base, nvals, grp.rank(), 32);
+    stage_update<PER, N3>(kp, U, dU, Uout, sr, base, nvals, grp.rank(), 32);
   } else {
     for (int i = grp.rank(); i < nvals; i += 32) Rout[base + i] = sr[i];
   }

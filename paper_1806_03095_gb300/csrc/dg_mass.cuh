@@ -1,9 +1,10 @@
 // Inverse mass (Sec. 2.3) and, optionally, the 2N stage update as a persistent, TMA-pipelined kernel.
 // The standalone M^{-1} (and the split organisation's M^{-1} + update) has little arithmetic per byte
 // in FP32, so it is bound by how many bytes each SM keeps in flight: every CTA streams batches of CB
-// consecutive cells (one contiguous range) into shared memory with cp.async.bulk, double-buffered on
-// two mbarriers, so that the copy of batch i+1 overlaps the sweeps of batch i.  Waits are bounded:
-// after kWaitPolls unsuccessful polls the kernel sets the context's error word and returns.
+// consecutive cells (one contiguous range) into shared memory with cp.async.bulk through a ring of NS
+// buffers and mbarriers, so that the copies of batches i+1 .. i+NS-1 are in flight while batch i is
+// swept.  Waits are bounded: after kWaitPolls unsuccessful polls the kernel sets the context's error
+// word and returns.
 #pragma once
 #include <cstdint>
 
@@ -64,18 +65,25 @@ constexpr int mass_tma_table_elems() {
   return (int)(((table_elems<N, QC, QV>() * sizeof(T) + 15) / 16) * 16 / sizeof(T));
 }
 
-template <typename T, int N, int QC, int QV, bool STAGE>
-constexpr size_t mass_tma_bytes(int cb) {
-  const size_t BV = (size_t)cb * 5 * N * N * N;
-  return 16 + (STAGE ? 2 * BV * 8 : 0) + mass_tma_table_elems<T, N, QC, QV, STAGE>() * sizeof(T) +
-         (2 * BV + (STAGE ? 2 * BV : 0) + BV + 2 * BV) * sizeof(T);
+// Pipeline depth: FP32 needs more bytes in flight per SM (its sweeps are short); FP64 is ALU-bound.
+template <typename T>
+constexpr int mass_tma_stages() {
+  return sizeof(T) == 4 ? 4 : 2;
 }
 
-// Cells per batch: the largest CB <= 8 with the CTA's shared memory below ~56 KB (4 CTAs per SM).
+template <typename T, int N, int QC, int QV, bool STAGE>
+constexpr size_t mass_tma_bytes(int cb) {
+  constexpr int NS = mass_tma_stages<T>();
+  const size_t BV = (size_t)cb * 5 * N * N * N;
+  return 8 * NS + 16 + (STAGE ? NS * BV * 8 : 0) + mass_tma_table_elems<T, N, QC, QV, STAGE>() * sizeof(T) +
+         (NS * BV + (STAGE ? NS * BV : 0) + BV + 2 * BV) * sizeof(T);
+}
+
+// Cells per batch: the largest CB <= 8 with the CTA's shared memory below ~75 KB (3 CTAs per SM).
 template <typename T, int N, int QC, int QV, bool STAGE>
 constexpr int mass_tma_cells() {
   int cb = 8;
-  while (cb > 1 && mass_tma_bytes<T, N, QC, QV, STAGE>(cb) > 56 * 1024) --cb;
+  while (cb > 1 && mass_tma_bytes<T, N, QC, QV, STAGE>(cb) > 75 * 1024) --cb;
   return cb;
 }
 
@@ -87,21 +95,22 @@ template <typename T, int N, int QC, int QV, int CB, bool STAGE, int GEO>
 __global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams kp, const double* U, const T* Rin,
                                                                    T* Rout, T* dU, double* Uout) {
   constexpr int N3 = N * N * N, CV = 5 * N3, BV = CB * CV;
+  constexpr int NS = mass_tma_stages<T>();
+  constexpr int HDR = ((8 * NS + 15) / 16) * 16;  // barriers, padded to 16 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  double* bufU = reinterpret_cast<double*>(smem_raw + 16);  // STAGE: [2][BV]
-  T* stab = reinterpret_cast<T*>(smem_raw + 16 + (STAGE ? 2 * BV * 8 : 0));
-  T* bufR = stab + mass_tma_table_elems<T, N, QC, QV, STAGE>();  // [2][BV]
-  T* bufD = bufR + 2 * BV;                                        // STAGE: [2][BV]
-  T* sr = bufD + (STAGE ? 2 * BV : 0);                            // result [BV]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);        // [NS]
+  double* bufU = reinterpret_cast<double*>(smem_raw + HDR);     // STAGE: [NS][BV]
+  T* stab = reinterpret_cast<T*>(smem_raw + HDR + (STAGE ? NS * BV * 8 : 0));
+  T* bufR = stab + mass_tma_table_elems<T, N, QC, QV, STAGE>();  // [NS][BV]
+  T* bufD = bufR + NS * BV;                                       // STAGE: [NS][BV]
+  T* sr = bufD + (STAGE ? NS * BV : 0);                           // result [BV]
   T* ma = sr + BV;                                                // sweep arena [2 BV]
   const int nbatch = (kp.Nc + CB - 1) / CB;
   if ((int)blockIdx.x >= nbatch) return;
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
   const bool readD = STAGE && kp.A != 0.0;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -115,15 +124,19 @@ __global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams
       if (readD) bulk_load(bufD + slot * BV, dU + (size_t)e0 * CV, bt, &bar[slot]);
     }
   };
-  if (threadIdx.x == 0) issue(blockIdx.x, 0);
+  // prologue: the first NS-1 batches of this CTA
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NS - 1; ++q)
+      if ((int)blockIdx.x + q * (int)gridDim.x < nbatch) issue(blockIdx.x + q * gridDim.x, q);
   int it = 0;
   bool timed_out = false;
   for (int b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
-    const int slot = it & 1;
-    const int bn = b + gridDim.x;
-    if (threadIdx.x == 0 && bn < nbatch) issue(bn, slot ^ 1);  // slot^1 was released at the end of it-1
+    const int slot = it % NS;
+    // batch it+NS-1 goes into the slot released at the end of iteration it-1
+    const int bn = b + (NS - 1) * gridDim.x;
+    if (threadIdx.x == 0 && bn < nbatch) issue(bn, (it + NS - 1) % NS);
     const int e0 = b * CB, nb = min(CB, kp.Nc - e0);
-    const bool ok = mbar_wait(&bar[slot], (uint32_t)((it >> 1) & 1));
+    const bool ok = mbar_wait(&bar[slot], (uint32_t)((it / NS) & 1));
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
@@ -147,11 +160,13 @@ __global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams
     __syncthreads();
   }
   if (timed_out) {
-    // give the copies still in flight a bounded chance to land before the CTA exits
+    // give the copies still in flight (iterations it .. it+NS-1) a bounded chance to land before the CTA exits
     if (threadIdx.x == 0) {
       atomicExch(kp.err, 1);
-      mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1));
-      mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
+      for (int q = 0; q < NS; ++q) {
+        const int j = it + q;
+        if ((int)blockIdx.x + j * (int)gridDim.x < nbatch) mbar_wait(&bar[j % NS], (uint32_t)((j / NS) & 1));
+      }
     }
     __syncthreads();
   }

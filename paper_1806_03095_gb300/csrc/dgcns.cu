@@ -260,6 +260,7 @@ struct dgcns_ctx {
   double* d_tau = nullptr;
   void* d_R = nullptr;        // residual scratch (split kernels)
   float* d_dev = nullptr;     // FP32 deviation state U - U_ref (mixed form)
+  float* d_dev2 = nullptr;    // second deviation buffer: the one a stage writes inside dg_cns_rk_steps
   void* d_fb = nullptr;       // face shares [Nc][6][2][5][N^2] (face-centric organisation)
   double* g64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stored geometry, FP64 (gcc gcv gfc gfv gm)
   void* d_xyz = nullptr;  // node coordinates in the residual precision (geometry on the fly)
@@ -452,6 +453,8 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   const size_t fb_bytes = (size_t)c->Nc * 60 * N * N * (prm->precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
   if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess ||
       (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess) ||
+      (prm->precision == DGCNS_MIXED && prm->kernel != DGCNS_KERNEL_SPLIT &&
+       cudaMalloc(&c->d_dev2, c->state_elems * sizeof(float)) != cudaSuccess) ||
       (prm->kernel == DGCNS_KERNEL_FACES && cudaMalloc(&c->d_fb, fb_bytes) != cudaSuccess)) {
     cudaGetLastError();
     dg_cns_destroy(c);
@@ -619,6 +622,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_tau);
   cudaFree(c->d_R);
   cudaFree(c->d_dev);
+  cudaFree(c->d_dev2);
   cudaFree(c->d_fb);
   cudaFree(c->d_xyz);
   for (const auto& t : c->pending) {
@@ -754,9 +758,12 @@ static int prep_dev(dgcns_ctx* c, KParams& kp, const double* U) {
   return DGCNS_OK;
 }
 
+// kp.Udev already set (multi-step calls of the mixed form): the deviation state is current.
 static int eval_L(dgcns_ctx* c, KParams kp, const double* U, void* dst, void* dU, double* Uout) {
-  const int rd = prep_dev(c, kp, U);
-  if (rd) return rd;
+  if (kp.Udev == nullptr) {
+    const int rd = prep_dev(c, kp, U);
+    if (rd) return rd;
+  }
   if (c->prm.kernel == DGCNS_KERNEL_FUSED) return run_op(c, OP_CELL | OP_FACE | OP_MASS, kp, U, nullptr, dst, dU, Uout);
   if (c->prm.kernel == DGCNS_KERNEL_FACES) {
     const int rf = run_faces(c, kp, U);
@@ -835,9 +842,33 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
   if (!U || !U_tmp || !dU || U == U_tmp) return fail(c, DGCNS_ERR_INVALID_ARG, "bad work arrays");
   double* a = U;
   double* b = U_tmp;
+  // Mixed form (fused or face-centric kernels): the stage kernel also writes float(U_out - U_ref)
+  // into the second deviation buffer, so only the first stage of the call needs the pre-pass.
+  const bool chain = c->d_dev2 != nullptr && nsteps > 0;
+  float* dcur = c->d_dev;
+  float* dnxt = c->d_dev2;
+  if (chain) {
+    KParams kp0 = c->kp;
+    const int rd = prep_dev(c, kp0, U);
+    if (rd) return rd;
+  }
   for (int n = 0; n < nsteps; ++n)
     for (int s = 0; s < 5; ++s) {
-      const int r = dg_cns_rk_stage(c, s, dt, t0 + (n + RK_C[s]) * dt, a, dU, b);
+      int r;
+      if (chain) {
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+        KParams kp = c->kp;
+        kp.out_mode = 2;
+        kp.A = RK_A[s];
+        kp.B = RK_B[s];
+        kp.dt = dt;
+        kp.Udev = dcur;
+        kp.devOut = dnxt;
+        r = eval_L(c, kp, a, nullptr, dU, b);
+        std::swap(dcur, dnxt);
+      } else {
+        r = dg_cns_rk_stage(c, s, dt, t0 + (n + RK_C[s]) * dt, a, dU, b);
+      }
       if (r) return r;
       std::swap(a, b);
     }

@@ -220,6 +220,25 @@ def test_rk_stage_split_in_place_allowed_fused_rejected():
     assert ei.value.code == -1
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_mixed_rk_steps_chained_deviation_equals_stage_calls(kernel):
+    """Inside dg_cns_rk_steps the mixed form's stage kernel writes the next stage's FP32 deviation state
+    itself; it is the same rounding of the same FP64 state as the pre-pass of single stage calls, so two
+    steps agree bit for bit with ten dg_cns_rk_stage calls."""
+    g, op = pair((3, 2, 2), 3, precision=1, kernel=kernel)
+    U0 = inputs.tgv_state(op.xyz) + 1e-2 * inputs.uniform((op.mesh.Nc, 5, op.mesh.n ** 3), 22)
+    dt = 1e-3
+    Us = on_gpu(U0)
+    g.rk_steps(2, dt, 0.0, Us)
+    a, b, dU = on_gpu(U0), g.empty_state(), g.empty_residual()
+    for n in range(2):
+        for s in range(5):
+            g.rk_stage(s, dt, n * dt, a, dU, b)
+            a, b = b, a
+    assert torch.equal(Us, a)
+    g.status()
+
+
 def test_rk_stage_face_centric_in_place():
     """The face-centric stage reads neighbours only in the face kernel, so U_out may alias U_in."""
     g, op = pair((2, 3, 2), 3, kernel=2)
