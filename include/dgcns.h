@@ -126,6 +126,21 @@ int dg_cns_sizes(const dgcns_ctx* ctx, int64_t* n_cells, int64_t* n_nodes, int64
  * (device, double).  Used to set initial conditions. */
 int dg_cns_node_coords(dgcns_ctx* ctx, double* xyz);
 
+/* Taylor-Green initial state (Sec. 4.2.1) at the LGL nodes, written to U (device, FP64,
+ * [n_cells][5][n^3]): u = U0 (sin x cos y cos z, -cos x sin y cos z, 0) with x = X / L, p = p0 +
+ * rho0 U0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2), uniform T0 = (U0 / Ma)^2 / (gamma R), rho = p / (R T0),
+ * rho E = rho (c_v T0 + |u|^2 / 2), with the context's gamma, R, Ma, rho0, U0, L.  Allocates and frees
+ * a temporary device buffer for the node coordinates; synchronizes the context's stream. */
+int dg_cns_set_initial_tgv(dgcns_ctx* ctx, double* U);
+
+/* Laminar channel start (Sec. 4.3.1) at the LGL nodes: rho = rho0, u1 = u_max (1 - y^2) + 0.05 u_max p1,
+ * u2 = 0.05 u_max p2, u3 = 0.05 u_max p3, rho E = rho0 (c_v T0 + |u|^2 / 2), T0 = (u_max / Ma)^2 / (gamma R),
+ * u_max = the context's u_mach (must be > 0).  The perturbations p in [-1, 1) come from the counter-based
+ * generator Philox4x32-10 (Salmon et al., SC'11) with key = seed: element i = (cell 3 + component) n^3 +
+ * node uses block i / 2 (counter (i / 2, 0, 0, 0)), output words (0, 1) for even i and (2, 3) for odd i,
+ * u = ((a >> 5) 2^26 + (b >> 6)) 2^-53, p = 2u - 1.  Same allocation and synchronization as above. */
+int dg_cns_set_initial_channel(dgcns_ctx* ctx, double* U, uint64_t seed);
+
 /* Evaluate one operator of Eq. SpatiallyDiscretizedProblem on U (device,
  * double [n_cells][5][n^3]) into R (device, residual type).  op is
  * DGCNS_OP_L, _F, _FC or _FV.  R must not alias U. */

@@ -22,6 +22,7 @@ NOALLOC_SCRATCH_BYTES = 16 << 20  # static device scratch of dg_cns_diagnostics_
 
 # Every symbol include/dgcns.h declares.
 EXPORTS = ("dg_cns_create", "dg_cns_destroy", "dg_cns_set_stream", "dg_cns_sizes", "dg_cns_node_coords",
+           "dg_cns_set_initial_tgv", "dg_cns_set_initial_channel",
            "dg_cns_apply", "dg_cns_inverse_mass", "dg_cns_rk_stage", "dg_cns_rk_steps", "dg_cns_diagnostics",
            "dg_cns_diagnostics_noalloc", "dg_cns_adjoint_apply", "dg_cns_rk_stage_adjoint",
            "dg_cns_kinetic_energy_gradient", "dg_cns_launch_count", "dg_cns_status", "dg_cns_timing", "dg_cns_kernel_times",
@@ -66,6 +67,8 @@ def load(path=LIB_PATH):
         "dg_cns_set_stream": ([vp, vp], ci),
         "dg_cns_sizes": ([vp, i64p, i64p, i64p], ci),
         "dg_cns_node_coords": ([vp, vp], ci),
+        "dg_cns_set_initial_tgv": ([vp, vp], ci),
+        "dg_cns_set_initial_channel": ([vp, vp, ctypes.c_uint64], ci),
         "dg_cns_apply": ([vp, vp, vp, ci], ci),
         "dg_cns_inverse_mass": ([vp, vp, vp], ci),
         "dg_cns_rk_stage": ([vp, ci, cd, cd, vp, vp, vp], ci),

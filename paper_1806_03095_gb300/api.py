@@ -178,6 +178,23 @@ class DGCNS:
         self._check(self.lib.dg_cns_launch_count(self.ctx, ctypes.byref(c)))
         return c.value
 
+    def dg_cns_set_initial_tgv(self, U=None):
+        """Taylor--Green initial state at the LGL nodes (computed on the GPU); returns U."""
+        U = self.empty_state() if U is None else self._state(U, "U")
+        self._sync_stream()
+        self._check(self.lib.dg_cns_set_initial_tgv(self.ctx, _ptr(U)))
+        return U
+
+    def dg_cns_set_initial_channel(self, seed, U=None):
+        """Laminar channel start with a Philox-seeded 5 % velocity perturbation (computed on the GPU)."""
+        U = self.empty_state() if U is None else self._state(U, "U")
+        self._sync_stream()
+        self._check(self.lib.dg_cns_set_initial_channel(self.ctx, _ptr(U), int(seed) & 0xFFFFFFFFFFFFFFFF))
+        return U
+
+    set_initial_tgv = dg_cns_set_initial_tgv
+    set_initial_channel = dg_cns_set_initial_channel
+
     def dg_cns_status(self):
         """Raise DGCNSError(TIMEOUT) if a kernel of this context gave up a bounded wait."""
         self._check(self.lib.dg_cns_status(self.ctx))

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "dg_common.h"
@@ -347,6 +348,85 @@ std::vector<double> host_node_coords(const dgcns_mesh& m, int k) {
 }
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// Initial states (dg_cns_set_initial_tgv / dg_cns_set_initial_channel)
+// ---------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, each
+// multiplying words 0 and 2 by the round multipliers, mixing the high halves with words 1 and 3 and
+// the key, permuting; the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Uniform in [0, 1) for element i: block i / 2 (counter (i / 2, 0, 0, 0), key = seed), words (0, 1) for
+// even i, (2, 3) for odd i, 53 bits as (a >> 5) 2^26 + (b >> 6).
+__device__ __forceinline__ double philox_u01(uint64_t i, uint64_t seed) {
+  const uint64_t j = i >> 1;
+  uint32_t c[4] = {(uint32_t)j, (uint32_t)(j >> 32), 0u, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t a = (i & 1) ? c[2] : c[0], b = (i & 1) ? c[3] : c[1];
+  const uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+  return (double)k * 0x1.0p-53;
+}
+
+// Channel start (Sec. 4.3.1): rho = rho0, u1 = u_max (1 - y^2) + a p1, u2 = a p2, u3 = a p3 with
+// a = 5 % u_max and p in [-1, 1) from Philox (element (cell 3 + component) n^3 + node); rho E =
+// rho0 (c_v T0 + |u|^2 / 2).  Every operation explicitly rounded, in a fixed order, so that the result
+// does not depend on contraction into FMAs.
+__global__ void init_channel_kernel(const double* __restrict__ xyz, double* __restrict__ U, int Nc, int N3,
+                                    uint64_t seed, double u_max, double amp_u, double e0, double rho0) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)Nc * N3;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = idx / N3, q = idx - e * N3;
+    const double y = xyz[(e * 3 + 1) * N3 + q];
+    double p[3];
+    for (int d = 0; d < 3; ++d) p[d] = __dadd_rn(-1.0, __dmul_rn(2.0, philox_u01((e * 3 + d) * N3 + q, seed)));
+    const double u1 = __dadd_rn(__dmul_rn(u_max, __dsub_rn(1.0, __dmul_rn(y, y))), __dmul_rn(amp_u, p[0]));
+    const double u2 = __dmul_rn(amp_u, p[1]), u3 = __dmul_rn(amp_u, p[2]);
+    const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(u1, u1), __dmul_rn(u2, u2)), __dmul_rn(u3, u3));
+    const double E = __dadd_rn(e0, __dmul_rn(0.5, s2));
+    double* o = U + e * 5 * N3 + q;
+    o[0] = rho0;
+    o[N3] = __dmul_rn(rho0, u1);
+    o[2 * N3] = __dmul_rn(rho0, u2);
+    o[3 * N3] = __dmul_rn(rho0, u3);
+    o[4 * N3] = __dmul_rn(rho0, E);
+  }
+}
+
+// Taylor--Green vortex (Sec. 4.2.1): u = U0 (sin x cos y cos z, -cos x sin y cos z, 0) with x = X / L,
+// p = p0 + rho0 U0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2), uniform T0 = (U0 / Ma)^2 / (gamma R),
+// rho = p / (R T0), rho E = rho (c_v T0 + |u|^2 / 2).
+__global__ void init_tgv_kernel(const double* __restrict__ xyz, double* __restrict__ U, int Nc, int N3, double U0,
+                                double Linv, double p0, double q0, double RT0, double e0) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)Nc * N3;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = idx / N3, q = idx - e * N3;
+    const double x = xyz[(e * 3) * N3 + q] * Linv, y = xyz[(e * 3 + 1) * N3 + q] * Linv,
+                 z = xyz[(e * 3 + 2) * N3 + q] * Linv;
+    const double u1 = U0 * sin(x) * cos(y) * cos(z), u2 = -U0 * cos(x) * sin(y) * cos(z);
+    const double p = p0 + q0 * (cos(2 * x) + cos(2 * y)) * (cos(2 * z) + 2.0);
+    const double rho = p / RT0;
+    double* o = U + e * 5 * N3 + q;
+    o[0] = rho;
+    o[N3] = rho * u1;
+    o[2 * N3] = rho * u2;
+    o[3 * N3] = 0.0;
+    o[4 * N3] = rho * (e0 + 0.5 * (u1 * u1 + u2 * u2));
+  }
+}
+
 extern "C" {
 
 int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream, dgcns_ctx** out) {
@@ -652,6 +732,52 @@ int dg_cns_sizes(const dgcns_ctx* c, int64_t* nc, int64_t* nn, int64_t* nd) {
   if (nn) *nn = (int64_t)c->Nc * c->N3;
   if (nd) *nd = (int64_t)c->Nc * c->N3 * 5;
   return DGCNS_OK;
+}
+
+// Node coordinates in a temporary device buffer (set-up calls only), then one initial-state kernel.
+static int with_device_coords(dgcns_ctx* c, const std::function<void(const double*)>& launch) {
+  const std::vector<double> host = host_node_coords(c->mesh, c->prm.k);
+  double* d = nullptr;
+  if (cudaMalloc(&d, host.size() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DGCNS_ERR_OOM, "out of device memory (node coordinates)");
+  }
+  int r = DGCNS_OK;
+  if (cudaMemcpyAsync(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess) {
+    r = cuda_fail(c, "node coordinates copy");
+  } else {
+    launch(d);
+    c->launches += 1;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+      r = cuda_fail(c, "initial-state kernel");
+  }
+  cudaFree(d);
+  return r;
+}
+
+int dg_cns_set_initial_tgv(dgcns_ctx* c, double* U) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U) return fail(c, DGCNS_ERR_INVALID_ARG, "U is NULL");
+  const dgcns_params& p = c->prm;
+  const double U0 = p.U0, c0 = U0 / p.Ma, T0 = c0 * c0 / (p.gamma * p.R), p0 = p.rho0 * p.R * T0;
+  const double q0 = p.rho0 * U0 * U0 / 16.0, cv = p.R / (p.gamma - 1.0);
+  return with_device_coords(c, [&](const double* xyz) {
+    init_tgv_kernel<<<2 * 152 * 8, 256, 0, c->stream>>>(xyz, U, c->Nc, c->N3, U0, 1.0 / p.L, p0, q0, p.R * T0,
+                                                         cv * T0);
+  });
+}
+
+int dg_cns_set_initial_channel(dgcns_ctx* c, double* U, uint64_t seed) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  if (!U) return fail(c, DGCNS_ERR_INVALID_ARG, "U is NULL");
+  const dgcns_params& p = c->prm;
+  if (!(p.u_mach > 0.0)) return fail(c, DGCNS_ERR_INVALID_ARG, "the channel start needs u_mach (u_max) > 0");
+  const double u_max = p.u_mach, cs = u_max / p.Ma, T0 = cs * cs / (p.gamma * p.R), cv = p.R / (p.gamma - 1.0);
+  const double amp_u = 0.05 * u_max, e0 = cv * T0;
+  return with_device_coords(c, [&](const double* xyz) {
+    init_channel_kernel<<<2 * 152 * 8, 256, 0, c->stream>>>(xyz, U, c->Nc, c->N3, seed, u_max, amp_u, e0, p.rho0);
+  });
 }
 
 int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {

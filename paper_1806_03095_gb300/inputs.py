@@ -12,11 +12,50 @@ c0 = U0/M, p0 = rho0 R T0, rho = p/(R T0), rho E = rho (c_v T0 + |u|^2/2).
 
 Channel (Sec. 4.3.1, laminar start): rho = 1, T = T0 = c^2/(gamma R) with
 c = u_max / M, u1 = u_max (1 - y^2) plus a seeded uniform perturbation of
-amplitude 5 % of u_max on every velocity component.
+amplitude 5 % of u_max on every velocity component, drawn from the counter-based
+generator Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), which libdgcns
+implements from the same definition (dg_cns_set_initial_channel), so both sides
+produce the same numbers.
 """
 import math
 
+import numpy as np
 import torch
+
+_PHILOX_M = (0xD2511F53, 0xCD9E8D57)  # round multipliers
+_PHILOX_W = (0x9E3779B9, 0xBB67AE85)  # key increments (Weyl sequence)
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10: counters ctr (4 arrays of uint32 words), key (k0, k1) -> 4 arrays of output words.
+
+    Each of the 10 rounds multiplies words 0 and 2 by the round multipliers (64-bit products split into
+    high and low halves), mixes the high halves with words 1 and 3 and the key, and permutes; the key is
+    bumped by the Weyl increments between rounds.
+    """
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(x, dtype=np.uint64) & mask for x in ctr]
+    k0, k1 = np.uint64(key[0]) & mask, np.uint64(key[1]) & mask
+    m0, m1 = np.uint64(_PHILOX_M[0]), np.uint64(_PHILOX_M[1])
+    for r in range(10):
+        p0, p1 = m0 * c[0], m1 * c[2]
+        c = [((p1 >> np.uint64(32)) ^ c[1] ^ k0) & mask, p1 & mask, ((p0 >> np.uint64(32)) ^ c[3] ^ k1) & mask,
+             p0 & mask]
+        k0, k1 = (k0 + np.uint64(_PHILOX_W[0])) & mask, (k1 + np.uint64(_PHILOX_W[1])) & mask
+    return c
+
+
+def philox_uniform(n, seed):
+    """n float64 uniforms in [0, 1): element i comes from block i // 2 (counter (i // 2, 0, 0, 0), key (seed mod
+    2^32, seed div 2^32)), words (0, 1) for even i and (2, 3) for odd i, as (a >> 5) 2^26 + (b >> 6) times 2^-53."""
+    nb = (int(n) + 1) // 2
+    j = np.arange(nb, dtype=np.uint64)
+    w = philox4x32([j & np.uint64(0xFFFFFFFF), j >> np.uint64(32), np.zeros(nb, np.uint64), np.zeros(nb, np.uint64)],
+                   (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF))
+    a = np.stack([w[0], w[2]], 1).reshape(-1)[:n]
+    b = np.stack([w[1], w[3]], 1).reshape(-1)[:n]
+    k = ((a >> np.uint64(5)) << np.uint64(26)) | (b >> np.uint64(6))
+    return torch.from_numpy(k.astype(np.float64) * 2.0 ** -53)
 
 
 def _gen(seed):
@@ -69,9 +108,11 @@ def tgv_state(xyz, gamma=1.4, R=287.0, Ma=0.1, rho0=1.0, U0=1.0, L=1.0):
 
 
 def channel_state(xyz, seed, u_max=18.3, Ma=0.1, gamma=1.4, R=287.0, rho0=1.0, amp=0.05):
-    """Laminar parabolic channel profile plus seeded 5 % uniform velocity perturbation."""
+    """Laminar parabolic channel profile plus a seeded 5 % uniform velocity perturbation in [-1, 1) (Philox,
+    element index (cell * 3 + component) * n^3 + node)."""
     y = xyz[:, 1]
-    pert = uniform((xyz.shape[0], 3, xyz.shape[2]), seed).to(xyz.device)
+    n = xyz.shape[0] * 3 * xyz.shape[2]
+    pert = (-1.0 + 2.0 * philox_uniform(n, seed)).reshape(xyz.shape[0], 3, xyz.shape[2]).to(xyz.device)
     u1 = u_max * (1.0 - y * y) + amp * u_max * pert[:, 0]
     u2 = amp * u_max * pert[:, 1]
     u3 = amp * u_max * pert[:, 2]

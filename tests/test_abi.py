@@ -79,6 +79,8 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dg_cns_launch_count(None, ctypes.byref(c)) == -1
     assert lib.dg_cns_timing(None, 1) == -1
     assert lib.dg_cns_status(None) == -1
+    assert lib.dg_cns_set_initial_tgv(None, None) == -1
+    assert lib.dg_cns_set_initial_channel(None, None, 1) == -1
     assert lib.dg_cns_kernel_times(None, None, None, 0) == -1
 
 

@@ -66,6 +66,26 @@ def test_node_coords_match_oracle():
     assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
 
 
+def test_set_initial_tgv_matches_closed_form():
+    """dg_cns_set_initial_tgv against the closed-form field of the input module at the same nodes
+    (sin/cos of the GPU and of the host may differ in the last bit)."""
+    g, op = pair((3, 2, 4), 3)
+    U = g.set_initial_tgv().cpu()
+    ref = inputs.tgv_state(op.xyz)
+    l2, mx = rel_err(U, ref)
+    assert l2 < 1e-14 and mx < 1e-14, (l2, mx)
+
+
+@pytest.mark.parametrize("seed", [1806, (1 << 40) + 7])
+def test_set_initial_channel_matches_input_module_bitwise(seed):
+    """dg_cns_set_initial_channel and the input module draw the same Philox numbers and evaluate the same
+    formula with the same rounding: identical states, on the stretched channel mesh."""
+    g, op = pair_mapped((3, 4, 2), 3, 1, 1.8, **CHANNEL)
+    U = g.set_initial_channel(seed).cpu()
+    ref = inputs.channel_state(g.node_coords().cpu(), seed)
+    assert torch.equal(U, ref)
+
+
 # -- residual F(U), per term and combined ------------------------------------------------------------
 CASES = [((2, 2, 2), 1), ((2, 2, 2), 2), ((2, 2, 2), 3), ((3, 2, 4), 3), ((2, 2, 2), 4), ((2, 2, 2), 5),
          ((2, 2, 2), 6)]
