@@ -35,7 +35,7 @@ FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per cell and launch from one ncu capture of
-# a kernel kind on a TGV mesh larger than L2, with the digest of the library sources it was built from:
+# a kernel kind on a TGV mesh larger than L2, with the digest of the device-code sources it was built from:
 # (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
 # The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
 TRAFFIC = {
@@ -46,12 +46,24 @@ TRAFFIC = {
 }
 
 
+def kernel_digest():
+    """sha256 over the device-code sources (every csrc file but the host plan dgcns.cu) and the compile flags."""
+    import hashlib
+    from paper_1806_03095_gb300 import build
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(build.CSRC)):
+        if name.endswith((".cuh", ".h")) or name == "dg_inst.cu":
+            h.update(name.encode())
+            h.update(open(os.path.join(build.CSRC, name), "rb").read())
+    h.update(" ".join(build.ARCH + build.FLAGS).encode())
+    return h.hexdigest()
+
+
 def traffic_per_launch(kind, prec, N, QC, QV, Nc):
     entry = TRAFFIC.get((kind, prec, N, QC, QV))
     if entry is None:
         return None, None
-    from paper_1806_03095_gb300 import build
-    if build._sources_digest() != entry[1]:
+    if kernel_digest() != entry[1]:
         return None, entry[2] + " (kernel sources changed since the capture)"
     return entry[0] * Nc, entry[2]
 

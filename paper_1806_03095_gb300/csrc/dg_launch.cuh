@@ -24,15 +24,17 @@ namespace dgcns {
 
 // Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
 // memory stays below ~112 KB, so that two or more CTAs fit on one SM (228 KB).
-template <typename T, int N, int QC, int QV>
+template <typename T, int N, int QC, int QV, bool FACE = false>
 constexpr int cells_per_cta() {
   using S = Sizes<N, QC, QV>;
   constexpr int arena = S::CELL_ARENA > S::FACE_ARENA ? S::CELL_ARENA : S::FACE_ARENA;
   constexpr int per_cell = (3 * 5 * S::N3 + arena) * (int)sizeof(T) + 8;
   constexpr int cb = (112 * 1024 - table_elems<N, QC, QV>() * (int)sizeof(T)) / per_cell;
-  // FP64 at k >= 3: 2 cells per CTA (4 CTAs per SM hide more latency than 4 cells in 2 CTAs: the face-
-  // centric cell + stage kernel at k = 3 is 2.5 % faster, measured)
-  constexpr int cap = sizeof(T) == 4 ? 4 : (N >= 4 && DGCNS_FP64_CELL_CAP > 2 ? 2 : DGCNS_FP64_CELL_CAP);
+  // FP64 at k >= 3 without element-centric faces: 2 cells per CTA (4 CTAs per SM hide more latency than
+  // 4 cells in 2 CTAs: the face-centric cell + stage kernel at k = 3 is 2.5 % faster, measured; the fused
+  // kernel is 9 % slower with 2 cells, so it keeps the larger batch)
+  constexpr int cap = sizeof(T) == 4 ? 4
+                                     : (!FACE && N >= 4 && DGCNS_FP64_CELL_CAP > 2 ? 2 : DGCNS_FP64_CELL_CAP);
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
@@ -887,7 +889,7 @@ int launch_op_any(const KParams& kp, const double* U, const void* Rin, void* Rou
   if constexpr (WARP) {
     return launch_op_warp<T, N, QC, QV, CELL, FACE, MASS, GEO>(kp, U, Rin, Rout, dU, Uout, st);
   } else {
-    constexpr int CB = cells_per_cta<T, N, QC, QV>();
+    constexpr int CB = cells_per_cta<T, N, QC, QV, FACE>();
     return launch_op<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>(kp, U, Rin, Rout, dU, Uout, st);
   }
 }

@@ -32,10 +32,9 @@ def test_roofline_entry_takes_the_dominant_kernel():
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     key = ("faces", 0, 4, 5, 4)
     monkeypatch.setitem(bench.TRAFFIC, key, (1000.0, "digest-at-capture", "profiles/x.md"))
-    from paper_1806_03095_gb300 import build
-    monkeypatch.setattr(build, "_sources_digest", lambda: "digest-at-capture")
+    monkeypatch.setattr(bench, "kernel_digest", lambda: "digest-at-capture")
     assert bench.traffic_per_launch("faces", 0, 4, 5, 4, 10) == (10000.0, "profiles/x.md")
-    monkeypatch.setattr(build, "_sources_digest", lambda: "another")
+    monkeypatch.setattr(bench, "kernel_digest", lambda: "another")
     t, src = bench.traffic_per_launch("faces", 0, 4, 5, 4, 10)
     assert t is None and "changed" in src
     assert bench.traffic_per_launch("faces", 1, 4, 5, 4, 10) == (None, None)
