@@ -39,9 +39,9 @@ FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 # (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
 # The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
 TRAFFIC = {
-    ("faces", 0, 4, 5, 4): (15115.0, "6236133f09abd832d243a8d96f46039ed1e80a8e318bddd5382406d696191926",
+    ("faces", 0, 4, 5, 4): (15097.7, "5cce0469c46341529709dc1d896ea4944fee563c9e893698c8dba2e4a31bb624",
                             "profiles/dg_face_kernel_fp64_tgv48_k3_full.md"),
-    ("cell_stage", 0, 4, 5, 4): (17690.0, "6236133f09abd832d243a8d96f46039ed1e80a8e318bddd5382406d696191926",
+    ("cell_stage", 0, 4, 5, 4): (17680.6, "5cce0469c46341529709dc1d896ea4944fee563c9e893698c8dba2e4a31bb624",
                                  "profiles/dg_op_kernel_cell_stage_fp64_tgv48_k3_full.md"),
 }
 
