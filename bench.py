@@ -205,11 +205,15 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--kernel", choices=["fused", "split", "faces"], default="faces")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
+    ap.add_argument("--inverse-mass", action="store_true",
+                    help="time dg_cns_inverse_mass alone on the workload (one JSON line; not the step metric)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    if args.inverse_mass:
+        return inverse_mass_only(args)
 
     from paper_1806_03095_gb300 import configs, roofline
     device = local if torch.cuda.is_available() else None
@@ -452,6 +456,38 @@ def memory_bound_kernels(reps=20):
         del g, R, Y, ctx, bufs
         torch.cuda.empty_cache()
     return out
+
+
+def inverse_mass_only(args):
+    """dg_cns_inverse_mass alone on args.workload in args.precision: warm-up, then args.steps timed calls
+    (the library's per-kernel CUDA events); HBM and ALU rates of the kernel."""
+    from paper_1806_03095_gb300 import configs, inputs, roofline
+    torch.cuda.set_device(0)
+    prec = 1 if args.precision == "mixed" else 0
+    cfg = configs.WORKLOADS[args.workload](precision=prec, kernel=0)
+    g = configs.make_context(cfg, device=0)
+    N = cfg["k"] + 1
+    Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
+    R = inputs.uniform(g.shape, 5).to(device=0, dtype=g.rdtype)
+    Y = torch.empty_like(R)
+    for _ in range(args.warmup):
+        g.inverse_mass(R, Y)
+    g.timing(True)
+    for _ in range(args.steps):
+        g.inverse_mass(R, Y)
+    kt = g.kernel_times()
+    g.timing(False)
+    g.status()
+    ms = kt["mass"][0] / kt["mass"][1]
+    by = 2 * Nc * N ** 3 * 5 * (4 if prec else 8)
+    fl = roofline.mass_flops(N) * Nc
+    peak = FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS
+    hbm = load_peaks().get("hbm_gbs", 6800.0)
+    print(json.dumps({"kernel": "inverse mass alone", "workload": args.workload, "precision": args.precision,
+                      "launches": kt["mass"][1], "avg_ms": round(ms, 4), "hbm_gbs": round(by / ms / 1e6, 1),
+                      "hbm_frac": round(by / ms / 1e6 / hbm, 4), "tflops": round(fl / ms / 1e9, 3),
+                      "alu_frac": round(fl / ms / 1e9 / peak, 4)}), flush=True)
+    return 0
 
 
 def k_sweep(steps=2):

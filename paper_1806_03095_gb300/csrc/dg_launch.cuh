@@ -21,6 +21,9 @@ namespace dgcns {
 #ifndef DGCNS_FP64_FACE_CAP
 #define DGCNS_FP64_FACE_CAP 8
 #endif
+#ifndef DGCNS_FP64_FACE_THREADS
+#define DGCNS_FP64_FACE_THREADS 128
+#endif
 
 // Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
 // memory stays below ~112 KB, so that two or more CTAs fit on one SM (228 KB).
@@ -1020,8 +1023,14 @@ constexpr int faces_per_cta() {
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
+// Threads per CTA of the CTA-wide face kernel.
+template <typename T>
+constexpr int face_threads() {
+  return sizeof(T) == 8 ? DGCNS_FP64_FACE_THREADS : op_threads<T>();
+}
+
 template <typename T, int N, int QC, int QV, int CB, int GEO>
-__global__ void __launch_bounds__(op_threads<T>()) dg_face_kernel(const KParams kp, const double* __restrict__ U,
+__global__ void __launch_bounds__(face_threads<T>()) dg_face_kernel(const KParams kp, const double* __restrict__ U,
                                                                   T* __restrict__ FB) {
   using S = Sizes<N, QC, QV>;
   constexpr int N3 = S::N3;
@@ -1230,7 +1239,7 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
       attr = true;
     }
     const dim3 grid((kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
-    k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
+    k<<<grid, face_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
