@@ -22,7 +22,7 @@ namespace dgcns {
 #define DGCNS_FP64_FACE_CAP 8
 #endif
 #ifndef DGCNS_FP64_FACE_THREADS
-#define DGCNS_FP64_FACE_THREADS 128
+#define DGCNS_FP64_FACE_THREADS 256
 #endif
 
 // Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
@@ -1023,7 +1023,8 @@ constexpr int faces_per_cta() {
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
-// Threads per CTA of the CTA-wide face kernel.
+// Threads per CTA of the CTA-wide face kernel (FP64, 8 faces per CTA at k = 3: 256 threads 8 % faster
+// than 128, measured; 160 and 192 in between).
 template <typename T>
 constexpr int face_threads() {
   return sizeof(T) == 8 ? DGCNS_FP64_FACE_THREADS : op_threads<T>();
