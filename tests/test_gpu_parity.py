@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 FP64 form: every output within 1e-12 relative (2-norm and max-norm over all
-5N entries), the tolerance of the operator statement.  Mixed form: the error
-bound derived in the design doc for FP32 cell/face arithmetic (tested loosely here,
-measured precisely by bench.py's precision report).
+5N entries), the tolerance of the operator statement (for smooth states the
+larger of 1e-12 and 4x the oracle's own sensitivity to a one-ulp change of U).
+Mixed form: a loose bound on the error of FP32 cell/face arithmetic on these
+small states (its size at full scale is measured by bench.py's extras).
 """
 import math
 
