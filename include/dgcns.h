@@ -116,10 +116,11 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* params, void* stre
 /* Free every buffer of the context (synchronises its stream first). */
 int dg_cns_destroy(dgcns_ctx* ctx);
 
-/* Replace the stream used by later calls. */
+/* Replace the stream used by later calls.  (Library utility, no counterpart in the paper.) */
 int dg_cns_set_stream(dgcns_ctx* ctx, void* stream);
 
-/* Host outputs: number of cells, nodes (n_cells (k+1)^3) and DoFs (5 nodes). */
+/* Host outputs: number of cells, nodes (n_cells (k+1)^3) and DoFs (5 nodes; the DoF count of
+ * Sec. 3, five conserved fields per node). */
 int dg_cns_sizes(const dgcns_ctx* ctx, int64_t* n_cells, int64_t* n_nodes, int64_t* n_dofs);
 
 /* Node coordinates of the degree-k geometry, written to xyz [n_cells][3][n^3]
@@ -215,12 +216,14 @@ int dg_cns_diagnostics(dgcns_ctx* ctx, const double* U, const void* L_of_U, doub
 #define DGCNS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int dg_cns_diagnostics_noalloc(dgcns_ctx* ctx, const double* U, const void* L_of_U, double* out_dev);
 
-/* Number of CUDA kernels this context has launched so far (host counter). */
+/* Number of CUDA kernels this context has launched so far (host counter; library utility, no
+ * counterpart in the paper). */
 int dg_cns_launch_count(const dgcns_ctx* ctx, int64_t* count);
 
 /* Synchronizes the context's stream and reports whether any kernel of this context gave up a
    bounded wait (its pipelined copies did not land within the poll limit) since the last call:
-   DGCNS_ERR_TIMEOUT then (the affected results are invalid), else DGCNS_OK.  The flag is cleared. */
+   DGCNS_ERR_TIMEOUT then (the affected results are invalid), else DGCNS_OK.  The flag is cleared.
+   (Library utility, no counterpart in the paper.) */
 int dg_cns_status(dgcns_ctx* ctx);
 
 /* Kernel kinds of the per-kernel timing. */
@@ -239,7 +242,7 @@ int dg_cns_status(dgcns_ctx* ctx);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around every kernel the
    context launches.  enable != 0 clears the totals and starts timing; enable == 0 stops it (the
-   totals are kept).  Off by default. */
+   totals are kept).  Off by default.  (Library utility, no counterpart in the paper.) */
 int dg_cns_timing(dgcns_ctx* ctx, int enable);
 
 /* Synchronizes the context's stream, then writes for kinds 0..n-1 (n <= DGCNS_KT_COUNT) the total
@@ -247,7 +250,8 @@ int dg_cns_timing(dgcns_ctx* ctx, int enable);
    enabled.  Either pointer may be NULL. */
 int dg_cns_kernel_times(dgcns_ctx* ctx, double* ms, int64_t* counts, int n);
 
-/* Message of the last error on this context (static string if ctx is NULL). */
+/* Message of the last error on this context (static string if ctx is NULL; the message of a failed
+ * dg_cns_create when ctx is NULL).  (Library utility, no counterpart in the paper.) */
 const char* dg_cns_last_error(const dgcns_ctx* ctx);
 
 #ifdef __cplusplus
