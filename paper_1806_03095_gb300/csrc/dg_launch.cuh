@@ -1023,15 +1023,16 @@ constexpr int faces_per_cta() {
   return cb < 1 ? 1 : (cb > cap ? cap : cb);
 }
 
-// Threads per CTA of the CTA-wide face kernel (FP64, 8 faces per CTA at k = 3: 256 threads 8 % faster
-// than 128, measured; 160 and 192 in between).
-template <typename T>
+// Threads per CTA of the CTA-wide face kernel.  FP64 affine, 8 faces per CTA at k = 3: 256 threads 8 %
+// faster than 128 (160 and 192 in between), measured; the non-affine variants hold fewer faces per CTA
+// and were slower with 256 (channel 32^3: -5 % stored, -30 % on the fly), so they keep 128.
+template <typename T, int GEO>
 constexpr int face_threads() {
-  return sizeof(T) == 8 ? DGCNS_FP64_FACE_THREADS : op_threads<T>();
+  return sizeof(T) == 8 ? (GEO == GEO_AFFINE ? DGCNS_FP64_FACE_THREADS : 128) : op_threads<T>();
 }
 
 template <typename T, int N, int QC, int QV, int CB, int GEO>
-__global__ void __launch_bounds__(face_threads<T>()) dg_face_kernel(const KParams kp, const double* __restrict__ U,
+__global__ void __launch_bounds__(face_threads<T, GEO>()) dg_face_kernel(const KParams kp, const double* __restrict__ U,
                                                                   T* __restrict__ FB) {
   using S = Sizes<N, QC, QV>;
   constexpr int N3 = S::N3;
@@ -1240,7 +1241,7 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
       attr = true;
     }
     const dim3 grid((kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
-    k<<<grid, face_threads<T>(), smem, st>>>(kp, U, static_cast<T*>(FB));
+    k<<<grid, face_threads<T, GEO>(), smem, st>>>(kp, U, static_cast<T*>(FB));
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
