@@ -71,6 +71,37 @@ def test_create_validates_on_host(lib):
     assert lib.dg_cns_create(None, None, None, ctypes.byref(ctx)) == -1
 
 
+def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
+    m, p = _lib.Mesh(), _lib.Params()
+    for d in range(3):
+        m.n[d], m.lo[d], m.hi[d], m.periodic[d] = 2, 0.0, 1.0, 1
+    m.mapping, m.map_param = mapping, (1.8 if mapping == 1 else 0.05)
+    if mapping == 1:
+        m.periodic[1], m.lo[1] = 0, -1.0
+    p.k, p.nq_conv, p.nq_visc = k, qc, qv
+    p.gamma, p.Pr, p.Re, p.Ma, p.R, p.rho0, p.U0, p.L = 1.4, 0.71, 1600.0, 0.1, 287.0, 1.0, 1.0, 1.0
+    p.precision, p.kernel, p.geometry = precision, kernel, geometry
+    return m, p
+
+
+@pytest.mark.parametrize("case,code", [
+    (dict(k=1, qc=2, qv=2, precision=1), -2),            # mixed form not compiled at k = 1
+    (dict(k=1, qc=2, qv=2, mapping=1), -2),              # non-affine geometry not compiled at k = 1
+    (dict(k=2, qc=4, qv=3, mapping=2, geometry=1), -2),  # geometry on the fly only at k = 3
+    (dict(k=3, qc=6, qv=4), -2),                         # no instantiation for this quadrature pair
+    (dict(k=3, qc=5, qv=4, kernel=3), -1),               # unknown kernel organisation
+    (dict(k=3, qc=5, qv=4, geometry=2), -1),             # unknown geometry mode
+    (dict(k=3, qc=5, qv=4, precision=2), -1),            # unknown precision
+])
+def test_create_rejects_uncompiled_or_invalid_features_on_host(lib, case, code):
+    """The feature table of the instantiations answers before any device work."""
+    m, p = _mesh_params(**case)
+    ctx = ctypes.c_void_p()
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == code
+    assert ctx.value is None
+    assert lib.dg_cns_last_error(None)
+
+
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.dg_cns_destroy(None) == -1
     assert lib.dg_cns_apply(None, None, None, 0) == -1
