@@ -89,6 +89,77 @@ constexpr int mass_tma_cells() {
 
 constexpr int kMassThreads = 256;
 
+// One 1D line through a square even-odd operator table (the layout of the sweep tables: even part
+// OH x IH, odd part OH x IH, centre column when DIN is odd), input and output in registers.
+template <typename T, int DIN, int DOUT>
+__device__ __forceinline__ void eo_line(const T* __restrict__ E, const T (&x)[DIN], T (&y)[DOUT]) {
+  constexpr int IH = DIN / 2, OH = (DOUT + 1) / 2;
+  const T* A = E;
+  const T* B = E + OH * IH;
+  const T* C = E + 2 * OH * IH;
+  T xe[IH > 0 ? IH : 1], xo[IH > 0 ? IH : 1];
+#pragma unroll
+  for (int i = 0; i < IH; ++i) {
+    xe[i] = x[i] + x[DIN - 1 - i];
+    xo[i] = x[i] - x[DIN - 1 - i];
+  }
+#pragma unroll
+  for (int q = 0; q < OH; ++q) {
+    T e = (DIN & 1) ? C[q] * x[IH] : T(0);
+    T o = T(0);
+#pragma unroll
+    for (int i = 0; i < IH; ++i) {
+      e += A[q * IH + i] * xe[i];
+      o += B[q * IH + i] * xo[i];
+    }
+    y[q] = e + o;
+    if (!((DOUT & 1) && q == OH - 1)) y[DOUT - 1 - q] = e - o;
+  }
+}
+
+// M^{-1} of a batch (Sec. 2.3, M_e^{-1} = S^{-1} diag(1/(|J| w)) S^{-T}, the three 1D factors of each
+// commuting): S^{-T} along x, y; then per z-line, in registers, S^{-T} along z, the scaling and S^{-1}
+// along z; then S^{-1} along y, x, the last sweep writing to `out` (global memory or shared).  Five
+// passes through shared memory instead of the eight of the generic routine.
+template <typename T, int N, int CB, int GEO>
+__device__ void mass_apply(const T* in, T* Abuf, T* Bbuf, T* out, const Tab<T>& tb, const KParams& kp, int e0,
+                           int nb, bool negate) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  const int nbl = nb * 5;
+  sweep<T, 0, N, N, N, N, 1, false>(in, Abuf, tb.eSmiT, nbl);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, 1, false>(Abuf, Bbuf, tb.eSmiT, nbl);
+  __syncthreads();
+  const T sg = negate ? T(-1) : T(1);
+  const T detJ = kconst<T>(kp).detJ;
+  for (int l = threadIdx.x; l < nbl * N2; l += blockDim.x) {
+    const int blk = l / N2, r = l - blk * N2;
+    const T* ip = Bbuf + blk * N3 + r;
+    T x[N], y[N], z[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = ip[i * N2];
+    eo_line<T, N, N>(tb.eSmiT, x, y);
+    const T wxy = tb.wm[r % N] * tb.wm[r / N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T w = wxy * tb.wm[q];
+      if (GEO == GEO_AFFINE)
+        w *= detJ;
+      else
+        w *= static_cast<const T*>(kp.gm)[(size_t)(e0 + blk / 5) * N3 + r + q * N2];
+      y[q] *= sg / w;
+    }
+    eo_line<T, N, N>(tb.eSmi, y, z);
+    T* op = Abuf + blk * N3 + r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) op[i * N2] = z[i];
+  }
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, 1, false>(Abuf, Bbuf, tb.eSmi, nbl);
+  __syncthreads();
+  sweep<T, 0, N, N, N, N, 1, false>(Bbuf, out, tb.eSmi, nbl);
+}
+
 // out_mode 0/1: Rout = (-1 if out_mode 1) M^{-1} Rin;  STAGE (out_mode 2): dU <- A dU + dt (-M^{-1} Rin),
 // U_out <- U + B dU.  Rin may alias Rout, U may alias U_out (each batch is read before it is written).
 template <typename T, int N, int QC, int QV, int CB, bool STAGE, int GEO>
@@ -141,9 +212,11 @@ __global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams
       timed_out = true;
       break;
     }
-    inverse_mass<T, N, CB, GEO>(nullptr, sr, ma, tb, kp, e0, nb, kp.out_mode != 0, false, CtaGroup(), nullptr,
-                                nullptr, bufR + slot * BV);
     const size_t base = (size_t)e0 * CV;
+    // without the stage update the last sweep writes the result straight to global memory
+    mass_apply<T, N, CB, GEO>(bufR + slot * BV, ma, ma + BV, STAGE ? sr : Rout + base, tb, kp, e0, nb,
+                              kp.out_mode != 0);
+    __syncthreads();
     if (STAGE) {
       const T A = T(kp.A), dt = T(kp.dt);
       const double B = kp.B;
@@ -154,8 +227,6 @@ __global__ void __launch_bounds__(kMassThreads) dg_mass_tma_kernel(const KParams
         dU[base + i] = du;
         Uout[base + i] = uold[i] + B * double(du);
       }
-    } else {
-      for (int i = threadIdx.x; i < nb * CV; i += blockDim.x) Rout[base + i] = sr[i];
     }
     __syncthreads();
   }
