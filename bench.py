@@ -39,9 +39,9 @@ FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 # (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
 # The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
 TRAFFIC = {
-    ("faces", 0, 4, 5, 4): (15106.1, "e78228ae0321f42e21a09ced83ba639e361a590d9e585bbfc8f1a92e2040c78f",
+    ("faces", 0, 4, 5, 4): (15103.7, "908ebd0b7af2f3d6e49b1ac2b26c1030a17057255a1ae3b3c00640c63d7b56f0",
                             "profiles/dg_face_kernel_fp64_tgv48_k3_full.md"),
-    ("cell_stage", 0, 4, 5, 4): (17681.9, "e78228ae0321f42e21a09ced83ba639e361a590d9e585bbfc8f1a92e2040c78f",
+    ("cell_stage", 0, 4, 5, 4): (17680.0, "908ebd0b7af2f3d6e49b1ac2b26c1030a17057255a1ae3b3c00640c63d7b56f0",
                                  "profiles/dg_op_kernel_cell_stage_fp64_tgv48_k3_full.md"),
 }
 
