@@ -521,42 +521,50 @@ def k_sweep(steps=2):
     return out
 
 
+GOLDEN_DISSIPATION = os.path.join(ROOT, "tests", "golden", "tgv8_k5_dissipation.json")
+
+
 def dissipation_history(t_final=2.0, every=8):
-    """-de_k/dt over t in [0, 2] on TGV 8^3, k = 5 (the 8^3 subset of the 40^3 workload), FP64 (parity-tested
-    against the oracle) and mixed, from L(U) every `every` steps; the oracle itself anchors t = 0."""
+    """-de_k/dt over t in [0, 2] on TGV 8^3, k = 5 (the 8^3 subset of the 40^3 workload), FP64 and mixed, from
+    L(U) every `every` steps, against the oracle's curve stored in tests/golden (written by the committed
+    oracle-only script beside it, with the same time step and sampling)."""
     from paper_1806_03095_gb300 import api, configs, inputs
     device = torch.cuda.current_device()
     cfg64 = configs.tgv(8, 5, precision=0)
+    ref = None
+    dt = configs.time_step(cfg64)
+    nsteps = int(round(t_final / dt))
+    if os.path.exists(GOLDEN_DISSIPATION):
+        with open(GOLDEN_DISSIPATION) as f:
+            gold = json.load(f)
+        dt, every, nsteps = gold["dt"], gold["every"], gold["nsteps"]
+        ref = torch.tensor([r[4] for r in gold["samples"]], dtype=torch.float64)
     hist = {}
     for prec in (0, 1):
         g = configs.make_context(dict(cfg64, precision=prec), device=device)
         U = inputs.tgv_state(g.node_coords()).contiguous()
         Ut, dU = g.empty_state(), g.empty_residual()
-        dt = configs.time_step(cfg64)
-        nsteps = int(round(t_final / dt))
         vals = []
         for n in range(0, nsteps + 1, every):
             vals.append(float(g.diagnostics(U, g.apply(U, op=api.OP_L))[2]))
             if n + every <= nsteps:
-                res = run_stages(g, every, dt, n * dt, (U, Ut, dU))
-                if res.data_ptr() != U.data_ptr():
-                    U, Ut = Ut, U
+                run_stages(g, every, dt, n * dt, (U, Ut, dU))
         hist[prec] = torch.tensor(vals, dtype=torch.float64)
         del g
     a, b = hist[0], hist[1]
-    from oracle import diagnostics as odiag, physics as ph
-    from oracle.mesh import BoxMesh
-    from oracle.operator import DGOperator
-    mesh = BoxMesh((8, 8, 8), cfg64["lo"], cfg64["hi"], (1, 1, 1), 5)
-    op = DGOperator(mesh, ph.Physics.from_numbers(1600.0, 0.71, 0.1), cfg64["nq_conv"], cfg64["nq_visc"])
-    U0 = inputs.tgv_state(op.xyz)
-    o0 = float(odiag.diagnostics(op, U0, op.L(U0))[2])
-    return {"quantity": "-de_k/dt, TGV 8^3, k=5, t in [0, %g], sampled every %d steps (%d samples)"
-                        % (t_final, every, len(a)),
-            "rel_l2_mixed_vs_fp64": float(torch.linalg.norm(b - a) / torch.linalg.norm(a)),
-            "rel_max_mixed_vs_fp64": float((b - a).abs().max() / a.abs().max()),
-            "t0_oracle": o0, "t0_fp64": float(a[0]), "t0_mixed": float(b[0]),
-            "final_fp64": float(a[-1]), "final_mixed": float(b[-1])}
+
+    def rel(x, y):
+        return {"rel_l2": float(torch.linalg.norm(x - y) / torch.linalg.norm(y)),
+                "rel_max": float((x - y).abs().max() / y.abs().max())}
+
+    out = {"quantity": "-de_k/dt, TGV 8^3, k=5, t in [0, %g], dt %.6g, sampled every %d steps (%d samples)"
+                       % (nsteps * dt, dt, every, len(a)),
+           "mixed_vs_fp64": rel(b, a), "final_fp64": float(a[-1]), "final_mixed": float(b[-1])}
+    if ref is not None and len(ref) == len(a):
+        out["fp64_vs_oracle"] = rel(a, ref)
+        out["mixed_vs_oracle"] = rel(b, ref)
+        out["final_oracle"] = float(ref[-1])
+    return out
 
 
 def adjoint_cost(nsteps=200, every=20, kernel=2):

@@ -272,6 +272,32 @@ def test_rk_stage_face_centric_in_place():
     assert torch.equal(Ui, Uo) and torch.equal(dU1, dU2)
 
 
+def test_tgv_dissipation_rate_history_against_oracle():
+    """TGV 8^3, k = 5, to t = 2 (783 RK(5,4) steps): -de_k/dt every 8 steps against the oracle's history
+    stored in tests/golden (written by the oracle-only script beside it, same dt and sampling)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv8_k5_dissipation.json")
+    with open(path) as f:
+        gold = json.load(f)
+    dt, every, nsteps = gold["dt"], gold["every"], gold["nsteps"]
+    ref = torch.tensor([r[4] for r in gold["samples"]], dtype=torch.float64)
+    g, op = pair((8, 8, 8), 5, kernel=2)
+    U = on_gpu(inputs.tgv_state(op.xyz))
+    Ut, dU = g.empty_state(), g.empty_residual()
+    vals = []
+    for n in range(0, nsteps + 1, every):
+        vals.append(float(g.diagnostics(U, g.apply(U, op=api.OP_L))[2]))
+        if n + every <= nsteps:
+            g.rk_steps(every, dt, n * dt, U, Ut, dU)
+    got = torch.tensor(vals, dtype=torch.float64)
+    assert len(got) == len(ref)
+    assert abs(float(got[0] - ref[0])) <= 1e-12 * abs(float(ref[0]))
+    l2 = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+    mx = float((got - ref).abs().max() / ref.abs().max())
+    assert l2 < 1e-8 and mx < 1e-8, (l2, mx)
+
+
 @pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_tgv_8cubed_ten_rk_steps_fp64(kernel):
     """Taylor--Green 8^3, k = 3, one operator evaluation plus 10 RK(5,4) steps at CFL 0.4."""
