@@ -295,7 +295,7 @@ def test_tgv_dissipation_rate_history_against_oracle():
     assert abs(float(got[0] - ref[0])) <= 1e-12 * abs(float(ref[0]))
     l2 = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
     mx = float((got - ref).abs().max() / ref.abs().max())
-    assert l2 < 1e-8 and mx < 1e-8, (l2, mx)
+    assert l2 < 1e-10 and mx < 1e-10, (l2, mx)
 
 
 @pytest.mark.parametrize("kernel", [0, 1, 2])
