@@ -144,3 +144,39 @@ def test_golden_tgv_constants():
     assert abs(g["rho0"] * g["R"] * phys.T_wall - g["p0"]) < 1e-12
     assert abs(0.75 * phys.nu - g["eps_0"]) < 1e-18
     assert abs(phys.mu * phys.c_p / phys.lam - g["Pr"]) < 1e-14
+
+
+def test_dissipation_golden_reproduces_from_its_script():
+    """The stored oracle history (tests/golden/tgv8_k5_dissipation.json) is what its committed script
+    produces: rerun the oracle for the first 8 steps and compare the first two samples exactly."""
+    import json
+    import math
+    import os
+
+    from oracle import diagnostics as odiag
+    from oracle import physics as ph
+    from oracle import rk as ork
+    from oracle.mesh import BoxMesh
+    from oracle.operator import DGOperator
+    from paper_1806_03095_gb300 import inputs
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    gold = json.load(open(os.path.join(here, "tgv8_k5_dissipation.json")))
+    op = DGOperator(BoxMesh((8,) * 3, (-math.pi,) * 3, (math.pi,) * 3, (1, 1, 1), 5),
+                    ph.Physics.from_numbers(1600.0, 0.71, 0.1), 8, 6)
+    dt, every = gold["dt"], gold["every"]
+    U = inputs.tgv_state(op.xyz)
+    dU = U * 0.0
+    got = []
+    for n in range(every + 1):
+        LU = op.L(U)
+        if n % every == 0:
+            got.append([float(v) for v in odiag.diagnostics(op, U, LU)[:3]])
+        if n == every:
+            break
+        for i in range(ork.STAGES):
+            dU = ork.A[i] * dU + dt * (LU if i == 0 else op.L(U))
+            U = U + ork.B[i] * dU
+    # exact on one machine; 1e-12 leaves room for a different reduction order on another host
+    for s_got, row in zip(got, gold["samples"][:2]):
+        for a, b in zip(s_got, row[2:5]):
+            assert abs(a - b) <= 1e-12 * abs(b), (s_got, row)
