@@ -11,3 +11,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libdgcns")
     config.addinivalue_line("markers", "slow: takes more than ~20 s on the CPU")
+    config.addinivalue_line("markers", "full_size: runs the benchmark workload at full size (run after the small cases)")
+
+
+def pytest_collection_modifyitems(config, items):
+    """Full-size cases run after every small case (stable order otherwise)."""
+    items.sort(key=lambda it: it.get_closest_marker("full_size") is not None)
