@@ -109,8 +109,9 @@ typedef struct {
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
  * (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,
  * penalty per cell, geometry) and allocates the context's device buffers.
- * Errors: INVALID_ARG (sizes, physics), UNSUPPORTED (no instantiation for
- * (k, nq_conv, nq_visc)), OOM, CUDA.  *out is NULL on error. */
+ * Errors: INVALID_ARG (sizes: every n[d] >= 1 and at most 2^30 cells in all;
+ * physics), UNSUPPORTED (no instantiation for (k, nq_conv, nq_visc)), OOM,
+ * CUDA.  *out is NULL on error. */
 int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* params, void* stream, dgcns_ctx** out);
 
 /* Free every buffer of the context (synchronises its stream first). */

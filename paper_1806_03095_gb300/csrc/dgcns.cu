@@ -465,8 +465,12 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     return bad(DGCNS_ERR_INVALID_ARG, "unknown mapping");
   if (mesh->mapping == DGCNS_MAP_CHANNEL && !(mesh->map_param > 0.0))
     return bad(DGCNS_ERR_INVALID_ARG, "channel stretch factor must be positive");
-  const long long ncell = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
-  if (ncell > (1LL << 30)) return bad(DGCNS_ERR_INVALID_ARG, "too many cells");
+  // checked factor by factor, so that the product cannot overflow before the comparison
+  long long ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    ncell *= mesh->n[d];
+    if (ncell > (1LL << 30)) return bad(DGCNS_ERR_INVALID_ARG, "too many cells (more than 2^30)");
+  }
   const int N = k + 1;
   bool found = false;
   for (const Registry& r : kRegistry)

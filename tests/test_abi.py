@@ -71,6 +71,18 @@ def test_create_validates_on_host(lib):
     assert lib.dg_cns_create(None, None, None, ctypes.byref(ctx)) == -1
 
 
+@pytest.mark.parametrize("n", [(1025, 1024, 1024), (1 << 21, 1 << 21, 1 << 22), (2 ** 31 - 1,) * 3])
+def test_create_rejects_too_many_cells_on_host(lib, n):
+    """More than 2^30 cells is refused before any device work, also where the product of the three
+    counts would overflow 64 bits (2^21 * 2^21 * 2^22 = 2^64)."""
+    m, p = _mesh_params(3, 5, 4)
+    m.n[0], m.n[1], m.n[2] = n
+    ctx = ctypes.c_void_p()
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -1
+    assert ctx.value is None
+    assert b"too many cells" in lib.dg_cns_last_error(None)
+
+
 def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
     m, p = _lib.Mesh(), _lib.Params()
     for d in range(3):
