@@ -156,13 +156,14 @@ int dg_cns_inverse_mass(dgcns_ctx* ctx, const void* in, void* out);
 /* One stage (0..4) of the 2N RK(5,4) scheme:
  *   dU <- A_stage dU + dt L(U_in, t + C_stage dt);  U_out <- U_in + B_stage dU.
  * U_in, U_out: double; dU: residual type (read only when A_stage != 0).
- * Split kernels allow U_out == U_in; the fused kernel needs U_out != U_in
- * (neighbours read U_in), else INVALID_ARG. */
+ * Split and face-centric kernels allow U_out == U_in; the fused kernel needs
+ * U_out != U_in (neighbours read U_in), else INVALID_ARG.  dU must not alias
+ * U_in or U_out (INVALID_ARG). */
 int dg_cns_rk_stage(dgcns_ctx* ctx, int stage, double dt, double t, const double* U_in, void* dU, double* U_out);
 
 /* nsteps full RK(5,4) steps from time t0 with constant dt.  On return U holds
  * the new state; U_tmp (double, state sized) and dU (residual type) are
- * caller-provided work arrays. */
+ * caller-provided work arrays, all three distinct (else INVALID_ARG). */
 int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU);
 
 /* Adjoint (vector-Jacobian product) of the operator of dg_cns_apply(DGCNS_OP_L):

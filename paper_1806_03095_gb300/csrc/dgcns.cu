@@ -955,6 +955,7 @@ int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* 
   (void)t;  // the operator is autonomous (constant body force)
   if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
   if (!U_in || !dU || !U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if (dU == (const void*)U_in || dU == (const void*)U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "dU must not alias U_in or U_out");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
   if (c->prm.kernel == DGCNS_KERNEL_FUSED && U_in == U_out)
     return fail(c, DGCNS_ERR_INVALID_ARG, "fused kernel needs U_out != U_in");
@@ -969,7 +970,8 @@ int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* 
 int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(c, DGCNS_ERR_INVALID_ARG, "nsteps < 0");
-  if (!U || !U_tmp || !dU || U == U_tmp) return fail(c, DGCNS_ERR_INVALID_ARG, "bad work arrays");
+  if (!U || !U_tmp || !dU || U == U_tmp || dU == (const void*)U || dU == (const void*)U_tmp)
+    return fail(c, DGCNS_ERR_INVALID_ARG, "U, U_tmp and dU must be distinct non-NULL arrays");
   double* a = U;
   double* b = U_tmp;
   // Mixed form (fused or face-centric kernels): the stage kernel also writes float(U_out - U_ref)
