@@ -297,6 +297,17 @@ static int cuda_fail(dgcns_ctx* c, const char* what) {
   return fail(c, DGCNS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// A CUDA call of dg_cns_create failed: OOM when the device ran out of memory, else the CUDA error
+// (no device, driver mismatch, ...).  Releases the partly built context.
+static int create_fail(dgcns_ctx* c, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  const bool oom = e == cudaErrorMemoryAllocation;
+  g_create_err = std::string(oom ? "out of device memory (" : "CUDA error (") + what + ")" +
+                 (oom ? std::string() : std::string(": ") + cudaGetErrorString(e));
+  dg_cns_destroy(c);
+  return oom ? DGCNS_ERR_OOM : DGCNS_ERR_CUDA;
+}
+
 static size_t res_bytes(const dgcns_ctx* c) {
   return c->state_elems * (c->prm.precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
 }
@@ -432,6 +443,7 @@ extern "C" {
 int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream, dgcns_ctx** out) {
   if (!out) return DGCNS_ERR_INVALID_ARG;
   *out = nullptr;
+  g_create_err = "no error";
   if (!mesh || !prm) {
     g_create_err = "NULL mesh or params";
     return DGCNS_ERR_INVALID_ARG;
@@ -526,24 +538,19 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
 
   if (cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->d_tau, tau.size() * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    dg_cns_destroy(c);
-    return DGCNS_ERR_OOM;
-  }
-  cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMalloc(&c->d_tau, tau.size() * sizeof(double)) != cudaSuccess)
+    return create_fail(c, "tables");
+  if (cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return create_fail(c, "table upload");
   const size_t fb_bytes = (size_t)c->Nc * 60 * N * N * (prm->precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
   if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess ||
       (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess) ||
       (prm->precision == DGCNS_MIXED && prm->kernel != DGCNS_KERNEL_SPLIT &&
        cudaMalloc(&c->d_dev2, c->state_elems * sizeof(float)) != cudaSuccess) ||
-      (prm->kernel == DGCNS_KERNEL_FACES && cudaMalloc(&c->d_fb, fb_bytes) != cudaSuccess)) {
-    cudaGetLastError();
-    dg_cns_destroy(c);
-    return DGCNS_ERR_OOM;
-  }
+      (prm->kernel == DGCNS_KERNEL_FACES && cudaMalloc(&c->d_fb, fb_bytes) != cudaSuccess))
+    return create_fail(c, "residual, deviation and face buffers");
   KParams& kp = c->kp;
   kp.Nc = c->Nc;
   for (int d = 0; d < 3; ++d) {
@@ -575,30 +582,22 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     c->gsize[3] = (size_t)c->Nc * 6 * 13 * QV * QV;
     c->gsize[4] = (size_t)c->Nc * c->N3;
     for (int i = 0; i < 5; ++i)
-      if (cudaMalloc(&c->g64[i], c->gsize[i] * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        dg_cns_destroy(c);
-        g_create_err = "out of device memory (geometry)";
-        return DGCNS_ERR_OOM;
-      }
+      if (cudaMalloc(&c->g64[i], c->gsize[i] * sizeof(double)) != cudaSuccess) return create_fail(c, "geometry");
     std::vector<double> xyz = host_node_coords(*mesh, k);
     double* d_xyz = nullptr;
-    if (cudaMalloc(&d_xyz, xyz.size() * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      dg_cns_destroy(c);
-      g_create_err = "out of device memory (coordinates)";
-      return DGCNS_ERR_OOM;
+    if (cudaMalloc(&d_xyz, xyz.size() * sizeof(double)) != cudaSuccess) return create_fail(c, "coordinates");
+    if (cudaMemcpy(d_xyz, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      const int r = create_fail(c, "coordinate upload");
+      cudaFree(d_xyz);
+      return r;
     }
-    cudaMemcpy(d_xyz, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice);
     KParams kg = kp;
     kg.tables = c->d_tab64;
     double* d_vol = nullptr;
     if (cudaMalloc(&d_vol, (size_t)c->Nc * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
+      const int r = create_fail(c, "volumes");
       cudaFree(d_xyz);
-      dg_cns_destroy(c);
-      g_create_err = "out of device memory (volumes)";
-      return DGCNS_ERR_OOM;
+      return r;
     }
     const int rg = c->L.geom(kg, d_xyz, c->g64[0], c->g64[1], c->g64[2], c->g64[3], c->g64[4], c->d_tau, d_vol,
                              c->nu * (k + 1) * (k + 1), c->stream);
@@ -618,10 +617,8 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
         c->d_xyz = d_xyz;
       }
       if (!c->d_xyz) {
-        cudaGetLastError();
-        dg_cns_destroy(c);
-        g_create_err = "out of device memory (coordinates)";
-        return DGCNS_ERR_OOM;
+        cudaFree(d_vol);
+        return create_fail(c, "FP32 coordinates");
       }
     } else {
       cudaFree(d_xyz);
@@ -634,20 +631,15 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
       c->volume = v;
     }
     cudaFree(d_vol);
-    if (rg != 0 || se != cudaSuccess) {
-      g_create_err = rg == -2 ? "stored geometry not available for this (k, nq) (shared memory)" : "geometry kernel";
-      cudaGetLastError();
+    if (rg == -2) {
       dg_cns_destroy(c);
-      return rg == -2 ? DGCNS_ERR_UNSUPPORTED : DGCNS_ERR_CUDA;
+      g_create_err = "stored geometry not available for this (k, nq) (shared memory)";
+      return DGCNS_ERR_UNSUPPORTED;
     }
+    if (rg != 0 || se != cudaSuccess) return create_fail(c, "geometry kernel");
     if (prm->precision == DGCNS_MIXED) {
       for (int i = 0; i < 5; ++i) {
-        if (cudaMalloc(&c->g32[i], c->gsize[i] * sizeof(float)) != cudaSuccess) {
-          cudaGetLastError();
-          dg_cns_destroy(c);
-          g_create_err = "out of device memory (FP32 geometry)";
-          return DGCNS_ERR_OOM;
-        }
+        if (cudaMalloc(&c->g32[i], c->gsize[i] * sizeof(float)) != cudaSuccess) return create_fail(c, "FP32 geometry");
         d2f_kernel<<<1024, 256, 0, c->stream>>>(c->g64[i], c->g32[i], c->gsize[i]);
         c->launches += 1;
       }
@@ -679,21 +671,13 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   c->L.diag_fp64(kd, nullptr, nullptr, nullptr, &nblk, c->stream);
   c->diag_blocks = nblk;
   if (cudaMalloc(&c->d_partial, ((size_t)nblk + 1) * 10 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    dg_cns_destroy(c);
-    return DGCNS_ERR_OOM;
-  }
+      cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
+    return create_fail(c, "diagnostics scratch");
   if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    dg_cns_destroy(c);
-    return DGCNS_ERR_CUDA;
-  }
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return create_fail(c, "set-up");
   c->kp.err = c->d_err;
-  if (cudaGetLastError() != cudaSuccess) {
-    dg_cns_destroy(c);
-    return DGCNS_ERR_CUDA;
-  }
+  if (cudaPeekAtLastError() != cudaSuccess) return create_fail(c, "set-up launches");
   *out = c;
   return DGCNS_OK;
 }
