@@ -22,6 +22,19 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def cuda_device(device=None):
+    """The CUDA device a context runs on, with its index: None (torch's current device), an index, or a
+    CUDA device given as a string or torch.device ("cuda" alone means the current device)."""
+    if device is None or isinstance(device, int):
+        index = torch.cuda.current_device() if device is None else int(device)
+    else:
+        dev = torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("libdgcns runs on a CUDA device, not %s" % dev)
+        index = torch.cuda.current_device() if dev.index is None else dev.index
+    return torch.device("cuda", index)
+
+
 class DGCNS:
     """One operator context: dg_cns_create on construction, dg_cns_destroy on close()."""
 
@@ -31,7 +44,7 @@ class DGCNS:
         if not torch.cuda.is_available():
             raise RuntimeError("libdgcns needs a CUDA device (there is no CPU fallback)")
         self.lib = _lib.load()
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = cuda_device(device)
         m = _lib.Mesh()
         p = _lib.Params()
         for d in range(3):
