@@ -147,6 +147,26 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dg_cns_kernel_times(None, None, None, 0) == -1
 
 
+def test_plain_c_client_links_and_checks_the_host_contract(lib, tmp_path):
+    """tests/c_abi_client.c: a C99 program that includes only the header and links only the library."""
+    import shutil
+    import subprocess
+
+    import torch
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(LIB)
+    exe = tmp_path / "client"
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi_client.c"), "-L", libdir, "-ldgcns",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    p = subprocess.run([str(exe)] + (["gpu"] if torch.cuda.is_available() else []), stdout=subprocess.PIPE,
+                       stderr=subprocess.PIPE, text=True, timeout=120)
+    assert p.returncode == 0, p.stdout + p.stderr
+    assert p.stdout.splitlines()[-1] == "failures 0"
+
+
 def test_kernel_kinds_match_header():
     text = open(os.path.join(ROOT, "include", "dgcns.h")).read()
     kinds = dict((name.lower(), int(v)) for name, v in re.findall(r"#define DGCNS_KT_(\w+) (\d+)", text))
