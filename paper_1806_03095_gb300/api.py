@@ -6,6 +6,7 @@ CUDA stream.
 """
 import ctypes
 import math
+import numbers
 
 import numpy as np
 import torch
@@ -25,7 +26,7 @@ def _ptr(t):
 def cuda_device(device=None):
     """The CUDA device a context runs on, with its index: None (torch's current device), an index, or a
     CUDA device given as a string or torch.device ("cuda" alone means the current device)."""
-    if device is None or isinstance(device, int):
+    if device is None or isinstance(device, numbers.Integral):
         index = torch.cuda.current_device() if device is None else int(device)
     else:
         dev = torch.device(device)

@@ -1,11 +1,12 @@
 """CPU checks of the Python binding's host logic (no context is created without a GPU)."""
+import numpy as np
 import pytest
 import torch
 
 from paper_1806_03095_gb300 import api
 
 
-@pytest.mark.parametrize("arg,index", [(1, 1), ("cuda:2", 2), (torch.device("cuda", 3), 3)])
+@pytest.mark.parametrize("arg,index", [(1, 1), (np.int64(4), 4), ("cuda:2", 2), (torch.device("cuda", 3), 3)])
 def test_cuda_device_forms(arg, index):
     assert api.cuda_device(arg) == torch.device("cuda", index)
 
