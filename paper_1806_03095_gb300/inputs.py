@@ -85,6 +85,46 @@ def random_state(n_cells, n_nodes, seed, rho0=1.0, mom=0.1, rhoE0=178.5714285714
     return U
 
 
+def parity_state(ncells, n_nodes, seed, rho0=1.0, mom=0.1, rhoE0=178.57142857142858, amp=0.02, contrast=0.4):
+    """Random conserved state [cells, 5, n_nodes] on a box of ncells = (nx, ny, nz) cells (x fastest) whose
+    energy level alternates between face neighbours: rho E in rhoE0 (1 + contrast)(1 +- amp) on cells with
+    i + j + k even and rhoE0 (1 - contrast)(1 +- amp) on odd ones; rho in rho0 (1 +- amp), momentum in +-mom.
+
+    Nodal values are independent draws, so every face carries jumps; with an even cell count along each
+    periodic axis the two cells of every face differ in parity, so the sound speeds of the two traces are
+    separated by a wide margin at every face point.
+    """
+    nx, ny, nz = (int(v) for v in ncells)
+    r = uniform((nx * ny * nz, 5, n_nodes), seed)
+    e = torch.arange(nx * ny * nz)
+    odd = ((e % nx) + (e // nx) % ny + e // (nx * ny)) % 2
+    level = torch.where(odd == 0, 1.0 + contrast, 1.0 - contrast).to(torch.float64)
+    U = torch.empty_like(r)
+    U[:, 0] = rho0 * (1.0 + amp * r[:, 0])
+    U[:, 1:4] = mom * r[:, 1:4]
+    U[:, 4] = rhoE0 * level[:, None] * (1.0 + amp * r[:, 4])
+    return U
+
+
+def smooth_direction(xyz, seed, kmax=1):
+    """Seeded smooth velocity direction [Nc, 3, n^3] at node coordinates xyz [Nc, 3, n^3] of a 2 pi periodic
+    box: each component is sum_kappa (a cos(kappa . x) + b sin(kappa . x)) over the integer wave vectors
+    0 < |kappa|_inf <= kmax with standard-normal a, b, scaled to unit root-mean-square over all nodal
+    entries (a step h along it moves every nodal velocity by about h)."""
+    g = _gen(seed)
+    r = torch.arange(-kmax, kmax + 1, dtype=torch.float64)
+    kap = torch.cartesian_prod(r, r, r)
+    kap = kap[kap.abs().sum(1) > 0]
+    phase = torch.einsum("kd,edn->ekn", kap, xyz.double().cpu())
+    out = []
+    for _ in range(3):
+        a = torch.randn(kap.shape[0], generator=g, dtype=torch.float64)
+        b = torch.randn(kap.shape[0], generator=g, dtype=torch.float64)
+        out.append(torch.einsum("k,ekn->en", a, torch.cos(phase)) + torch.einsum("k,ekn->en", b, torch.sin(phase)))
+    v = torch.stack(out, 1)
+    return v / torch.sqrt((v * v).mean())
+
+
 def random_direction(shape, seed):
     """Seeded standard-normal array normalised to unit 2-norm (adjoint test directions)."""
     v = torch.randn(tuple(shape), generator=_gen(seed), dtype=torch.float64)

@@ -374,3 +374,112 @@ def test_oracle_tangent_linear_model_matches_finite_differences():
     h = 1e-6
     fd = (op.L(U + h * V) - op.L(U - h * V)) / (2 * h)
     assert float(torch.linalg.norm(JV - fd) / torch.linalg.norm(JV)) < 1e-7
+
+
+# -- body force (Sec. 2.1: F_rhs = (0, f, f.u)) -------------------------------------------------------------
+BF_PHYS = ph.Physics.from_numbers(180.0, 0.71, 0.1, u_mach=18.3, body_force=(0.7, -0.4, 1.3))
+
+
+def _linear_flow(xyz, rho=2.0):
+    """rho constant, u = a + B x (degree 1 in x, so degree k in the reference coordinates of a degree-k
+    isoparametric cell: the nodal field is exact), p from a constant temperature."""
+    a = torch.tensor([0.3, -1.1, 0.8], dtype=torch.float64)
+    B = torch.tensor([[0.5, -0.2, 0.1], [0.3, 0.4, -0.6], [-0.7, 0.2, 0.9]], dtype=torch.float64)
+    u = a[None, :, None] + torch.einsum("ab,ebn->ean", B, xyz)
+    U = torch.empty((xyz.shape[0], 5, xyz.shape[2]), dtype=torch.float64)
+    U[:, 0] = rho
+    U[:, 1:4] = rho * u
+    U[:, 4] = rho * (BF_PHYS.c_v * 300.0 + 0.5 * (u * u).sum(1))
+    return U, u, a, B
+
+
+def _body_force_pins_hold(op, mesh, centroid):
+    f = torch.tensor(BF_PHYS.body_force, dtype=torch.float64)
+    U, u, a, B = _linear_flow(torch.as_tensor(mesh.xyz))
+    Fr = op.body_force(U)
+    nodal = op.mass_solve(Fr)
+    # M^-1 (V, F_rhs): density row 0, momentum rows f, energy row f . u at every node (f . u lies in the
+    # space, and M and the load use the same k+1 point rule)
+    ok = bool(torch.allclose(nodal[:, 0], torch.zeros_like(nodal[:, 0]), atol=1e-12))
+    for d in range(3):
+        ok &= bool(torch.allclose(nodal[:, 1 + d], f[d].expand_as(nodal[:, 1 + d]), rtol=1e-12, atol=1e-12))
+    ok &= bool(torch.allclose(nodal[:, 4], torch.einsum("a,ean->en", f, u), rtol=1e-11, atol=1e-11))
+    # v = 1: the energy row sums to int f . u = |Omega| f . (a + B x_centroid)
+    if centroid is not None:
+        exact = mesh.volume() * float(f @ (a + B @ torch.as_tensor(centroid, dtype=torch.float64)))
+        ok &= abs(float(Fr[:, 4].sum()) - exact) <= 1e-12 * abs(exact)
+    return ok
+
+
+@pytest.mark.parametrize("mapping,A", [(MAP_AFFINE, 0.0), (MAP_CHANNEL, 1.8)])
+def test_body_force_rows(mapping, A):
+    """(V, F_rhs) with F_rhs = (0, f, f.u) on a linear flow at constant density 2: every nodal row of
+    M^{-1}(V, F_rhs) is its closed form, and on the affine box the energy row integrates to int f.u."""
+    mesh = BoxMesh((2, 3, 2), [0.0, -1.0, 0.0], [2.0, 1.0, 1.0], (1, 0, 1), 3, mapping, A)
+    op = make_op(mesh, BF_PHYS)
+    assert _body_force_pins_hold(op, mesh, (1.0, 0.0, 0.5) if mapping == MAP_AFFINE else None)
+
+
+@pytest.mark.parametrize("mistake", ["f.m", "sign"])
+def test_body_force_negative_control(monkeypatch, mistake):
+    """Planted mistakes in the energy row: f.m for f.u (a factor rho = 2 here) and a flipped sign."""
+    mesh = BoxMesh((2, 3, 2), [0.0, -1.0, 0.0], [2.0, 1.0, 1.0], (1, 0, 1), 3, MAP_AFFINE, 0.0)
+    op = make_op(mesh, BF_PHYS)
+    orig = DGOperator.body_force_cells
+
+    def planted(self, U, E, source=None, t=0.0):
+        r = orig(self, U, E, source, t)
+        r[:, 4] = r[:, 4] * (U[E][:, 0, :1] if mistake == "f.m" else -1.0)
+        return r
+
+    monkeypatch.setattr(DGOperator, "body_force_cells", planted)
+    assert not _body_force_pins_hold(op, mesh, (1.0, 0.0, 0.5))
+
+
+# -- isothermal no-slip wall: the mirror reading (Sec. 4.3.1) -----------------------------------------------
+def _wall_pins_hold(ghost):
+    """For random interior states: rho+ = rho-, the face averages are u = 0 and T = T_wall, and the LLF
+    mass flux through the wall, {{m}}.n + Lambda/2 (rho- - rho+), vanishes for any normal."""
+    phys = BF_PHYS
+    r = inputs.uniform((4096, 5), 31)
+    rho = 1.0 + 0.5 * r[:, 0]
+    u = 20.0 * r[:, 1:4]
+    T = phys.T_wall * (1.0 + 0.3 * r[:, 4])
+    Um = torch.cat([rho[:, None], rho[:, None] * u, (rho * (phys.c_v * T + 0.5 * (u * u).sum(1)))[:, None]], 1)
+    Up = ghost(Um, phys)
+    rp = Up[:, 0]
+    up = Up[:, 1:4] / rp[:, None]
+    Tp = (Up[:, 4] / rp - 0.5 * (up * up).sum(1)) / phys.c_v
+    n = inputs.uniform((4096, 3), 32)
+    n = n / torch.linalg.norm(n, dim=1, keepdim=True)
+    lam = torch.linalg.norm(u, dim=1) + ph.sound_speed(Um, phys.gamma)
+    mass_flux = 0.5 * ((Um[:, 1:4] + Up[:, 1:4]) * n).sum(1) + 0.5 * lam * (Um[:, 0] - rp)
+    return (bool(torch.equal(rp, rho)) and float((0.5 * (u + up)).abs().max()) < 1e-12
+            and float((0.5 * (T + Tp) - phys.T_wall).abs().max()) < 1e-9 * phys.T_wall
+            and float(mass_flux.abs().max()) < 1e-12)
+
+
+def test_wall_ghost_state_reading():
+    assert _wall_pins_hold(ph.wall_ghost_state)
+
+
+def test_wall_ghost_state_negative_controls():
+    """Planted mistakes: T+ = T_wall - T-, and a mirror of the first velocity component only."""
+    def state(rho, m, T, phys):
+        u = m / rho[:, None]
+        return torch.cat([rho[:, None], m, (rho * (phys.c_v * T + 0.5 * (u * u).sum(1)))[:, None]], 1)
+
+    def temperature(U, phys):
+        u = U[:, 1:4] / U[:, 0:1]
+        return (U[:, 4] / U[:, 0] - 0.5 * (u * u).sum(1)) / phys.c_v
+
+    def half_temperature(U, phys):
+        return state(U[:, 0], -U[:, 1:4], phys.T_wall - temperature(U, phys), phys)
+
+    def first_component_only(U, phys):
+        m = U[:, 1:4].clone()
+        m[:, 0] = -m[:, 0]
+        return state(U[:, 0], m, 2.0 * phys.T_wall - temperature(U, phys), phys)
+
+    assert not _wall_pins_hold(half_temperature)
+    assert not _wall_pins_hold(first_component_only)

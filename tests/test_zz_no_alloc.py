@@ -4,7 +4,8 @@ point).  Its partial sums live in a static device array; the test calls it throu
 twice in a row and checks both results against dg_cns_diagnostics, and checks that a mesh too
 large for the static scratch is refused before anything runs.
 
-This file is collected last on purpose (name), so a failure here comes after every other test."""
+tests/conftest.py sorts this file after every other test (full-size cases included), so a run that stops
+at its first failure has already run everything else when it reaches this file."""
 import ctypes
 import math
 
