@@ -106,8 +106,11 @@ typedef struct {
 #define DGCNS_GEO_STORED 0
 #define DGCNS_GEO_ON_THE_FLY 1
 
-/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
- * (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,
+/* Create a context on the current CUDA device.  Every later call with the
+ * context runs on that device whatever device is current when it is made: it
+ * makes the context's device current for the call and restores the caller's
+ * current device before it returns.  `stream` is a cudaStream_t of that
+ * device (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,
  * penalty per cell, geometry) and allocates the context's device buffers.
  * Errors: INVALID_ARG (sizes: every n[d] >= 1 and at most 2^30 cells in all;
  * physics), UNSUPPORTED (no instantiation for (k, nq_conv, nq_visc)), OOM,
@@ -145,7 +148,7 @@ int dg_cns_set_initial_channel(dgcns_ctx* ctx, double* U, uint64_t seed);
 
 /* Evaluate one operator of Eq. SpatiallyDiscretizedProblem on U (device,
  * double [n_cells][5][n^3]) into R (device, residual type).  op is
- * DGCNS_OP_L, _F, _FC or _FV.  R must not alias U. */
+ * DGCNS_OP_L, _F, _FC or _FV.  R must not overlap U (INVALID_ARG). */
 int dg_cns_apply(dgcns_ctx* ctx, const double* U, void* R, int op);
 
 /* out = M^-1 in (tensor-product inverse of the block-diagonal mass matrix,
@@ -157,22 +160,27 @@ int dg_cns_inverse_mass(dgcns_ctx* ctx, const void* in, void* out);
  *   dU <- A_stage dU + dt L(U_in, t + C_stage dt);  U_out <- U_in + B_stage dU.
  * U_in, U_out: double; dU: residual type (read only when A_stage != 0).
  * Split and face-centric kernels allow U_out == U_in; the fused kernel needs
- * U_out != U_in (neighbours read U_in), else INVALID_ARG.  dU must not alias
- * U_in or U_out (INVALID_ARG). */
+ * U_out != U_in (neighbours read U_in), else INVALID_ARG.  Otherwise no two of
+ * U_in, U_out and dU may overlap, views at an offset included (INVALID_ARG). */
 int dg_cns_rk_stage(dgcns_ctx* ctx, int stage, double dt, double t, const double* U_in, void* dU, double* U_out);
 
 /* nsteps full RK(5,4) steps from time t0 with constant dt.  On return U holds
  * the new state; U_tmp (double, state sized) and dU (residual type) are
- * caller-provided work arrays, all three distinct (else INVALID_ARG). */
+ * caller-provided work arrays; no two of the three may overlap (else
+ * INVALID_ARG). */
 int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU);
 
 /* Adjoint (vector-Jacobian product) of the operator of dg_cns_apply(DGCNS_OP_L):
  *   G = (dL/dU)^T W = -(dF/dU)^T M^-1 W     (M symmetric)
  * evaluated by transposed sum factorization and transposed pointwise flux
- * Jacobians (LLF, F_c, F_v, the SIPG terms and the wall state), faces
- * element-centric.  Not in the paper (it is forward-only): the transpose of
+ * Jacobians (LLF, F_c, F_v, the SIPG terms and the wall state).  Faces follow
+ * the context's kernel organisation: face-centric (DGCNS_KERNEL_FACES, the
+ * default: every face once, both cells' shares through the face buffer) or
+ * element-centric (split and fused contexts: each cell transposes its own and
+ * its neighbours' face terms).  Not in the paper (it is forward-only): the transpose of
  * Eq. WeakFormulationConservedVariables as discretised here.  U: double state;
- * W, G: residual type; G must not alias U.  UNSUPPORTED with a body force. */
+ * W, G: residual type; G must not overlap U (INVALID_ARG); G may be W.
+ * UNSUPPORTED with a body force. */
 int dg_cns_adjoint_apply(dgcns_ctx* ctx, const double* U, const void* W, void* G);
 
 /* Adjoint of one stage of dg_cns_rk_stage (reverse of dU <- A dU + dt L(U_in),
@@ -180,11 +188,13 @@ int dg_cns_adjoint_apply(dgcns_ctx* ctx, const double* U, const void* W, void* G
  * are the adjoints of (U_out, dU after the stage); on return those of (U_in,
  * dU before the stage):  W = lam_dU + B lam_U;  lam_U += dt (dL/dU)^T W;
  * lam_dU = A W.  U_in is the stage's input state (recomputed from a
- * checkpoint by the caller).  Uses the context's residual scratch. */
+ * checkpoint by the caller).  Uses the context's residual scratch.  No two of
+ * U_in, lam_U and lam_dU may overlap (INVALID_ARG). */
 int dg_cns_rk_stage_adjoint(dgcns_ctx* ctx, int stage, double dt, const double* U_in, double* lam_U, void* lam_dU);
 
 /* G = d e_k / dU (double, state layout) for e_k of dg_cns_diagnostics: the
- * seed of the discrete adjoint of the final kinetic energy. */
+ * seed of the discrete adjoint of the final kinetic energy.  G must not
+ * overlap U (INVALID_ARG). */
 int dg_cns_kinetic_energy_gradient(dgcns_ctx* ctx, const double* U, double* G);
 
 /* Taylor--Green diagnostics of Sec. 4.2.3 in FP64 (Gauss rule nq_conv):

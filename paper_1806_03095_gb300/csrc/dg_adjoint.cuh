@@ -595,11 +595,8 @@ int adj_launch_geo(const KParams& kp, const double* U, const void* Y, void* G, d
   constexpr size_t smem = adj_smem_bytes<T, N, QC, QV, CB, PAIR>();
   if (smem > 227 * 1024) return -2;
   auto k = dg_adj_kernel<T, N, QC, QV, CB, GEO, PAIR>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   const int grid = (kp.Nc + CB - 1) / CB;
   k<<<grid, NT, smem, st>>>(kp, U, static_cast<const T*>(Y), static_cast<T*>(G), lamU);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

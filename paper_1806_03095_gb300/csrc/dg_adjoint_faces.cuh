@@ -391,11 +391,8 @@ int launch_adj_faces(const KParams& kp, const double* U, const void* Y, void* FB
   constexpr size_t smem = adj_face_smem_bytes<T, N, QC, QV, CB>();
   if (smem > 227 * 1024) return -2;
   auto k = dg_adj_face_kernel<T, N, QC, QV, CB, GEO>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   int extra = 0;
   for (int d = 0; d < 3; ++d) {
     if (kp.periodic[d]) continue;

@@ -1,5 +1,7 @@
 // Shared host/device declarations of libdgcns (not part of the public ABI).
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace dgcns {
@@ -116,5 +118,18 @@ void fill_kconst(const KParams& kp, KConst<T>& c) {
 }
 
 constexpr int GEO_AFFINE = 0, GEO_STORED = 1, GEO_FLY = 2;
+
+// Dynamic shared-memory attribute of a kernel: a per-device setting, made once per (kernel, device) on
+// the current device.  done[] is the kernel's own flag array (a static of its launcher).
+constexpr int kMaxDevices = 64;
+template <class K>
+inline int smem_attr_once(K kernel, size_t smem, bool* done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev >= 0 && dev < kMaxDevices && done[dev]) return 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  if (dev >= 0 && dev < kMaxDevices) done[dev] = true;
+  return 0;
+}
 
 }  // namespace dgcns

@@ -71,14 +71,35 @@ struct Tab {
   const T *wc, *wv, *wm, *dl0, *dl1;
 };
 
+// The same tables in constant memory, one copy per instantiation (and translation unit), written by
+// upload_const_tables when a context is created.  The sweeps index the 1D operators only with
+// compile-time offsets, so the FMAs take the coefficients as constant-bank operands: no load
+// instruction per coefficient (from shared memory that was one load per FMA, which bound the FP32
+// kernels by the shared-memory pipe).  Point weights and trace derivatives are indexed per lane and
+// stay in shared memory (the constant cache serialises lane-dependent addresses).
+template <typename T, int N, int QC, int QV>
+__constant__ T c_tab[make_layout(N, QC, QV).total];
+
+template <int N, int QC, int QV>
+int upload_const_tables(const double* t64, const float* t32, cudaStream_t st) {
+  constexpr int n = make_layout(N, QC, QV).total;
+  if (cudaMemcpyToSymbolAsync(c_tab<double, N, QC, QV>, t64, n * sizeof(double), 0, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyToSymbolAsync(c_tab<float, N, QC, QV>, t32, n * sizeof(float), 0, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return -1;
+  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : -1;
+}
+
 template <typename T, int N, int QC, int QV>
 __device__ __forceinline__ Tab<T> load_tables(const T* __restrict__ g, T* s) {
   constexpr TableLayout L = make_layout(N, QC, QV);
   for (int i = threadIdx.x; i < L.total; i += blockDim.x) s[i] = g[i];
+  const T* c = c_tab<T, N, QC, QV>;
   Tab<T> t;
-  t.eSc = s + L.eo[EO_SC]; t.eScT = s + L.eo[EO_SCT]; t.eDc = s + L.eo[EO_DC]; t.eDcT = s + L.eo[EO_DCT];
-  t.eSv = s + L.eo[EO_SV]; t.eSvT = s + L.eo[EO_SVT]; t.eDv = s + L.eo[EO_DV]; t.eDvT = s + L.eo[EO_DVT];
-  t.eSmi = s + L.eo[EO_SMI]; t.eSmiT = s + L.eo[EO_SMIT]; t.eSm = s + L.eo[EO_SM]; t.eDm = s + L.eo[EO_DM];
+  t.eSc = c + L.eo[EO_SC]; t.eScT = c + L.eo[EO_SCT]; t.eDc = c + L.eo[EO_DC]; t.eDcT = c + L.eo[EO_DCT];
+  t.eSv = c + L.eo[EO_SV]; t.eSvT = c + L.eo[EO_SVT]; t.eDv = c + L.eo[EO_DV]; t.eDvT = c + L.eo[EO_DVT];
+  t.eSmi = c + L.eo[EO_SMI]; t.eSmiT = c + L.eo[EO_SMIT]; t.eSm = c + L.eo[EO_SM]; t.eDm = c + L.eo[EO_DM];
   t.wc = s + L.wc; t.wv = s + L.wv; t.wm = s + L.wm; t.dl0 = s + L.dl0; t.dl1 = s + L.dl1;
   return t;
 }

@@ -625,11 +625,8 @@ int geom_launch(const KParams& kp, const double* xyz, double* gcc, double* gcv, 
   auto k = dg_geom_kernel<N, QC, QV>;
   constexpr size_t smem = (table_elems<N, QC, QV>() + 3 * N * N * N + geom_buf_elems<N, QC, QV>() + 8) * sizeof(double);
   if (smem > 227 * 1024) return -2;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   k<<<kp.Nc, NT, smem, st>>>(kp, xyz, gcc, gcv, gfc, gfv, gm, tau, vol, nu_kk);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }
@@ -698,11 +695,8 @@ int ekgrad_launch_geo(const KParams& kp, const double* U, double* G, double inv_
   constexpr size_t smem = (table_elems<N, QC, QV>() + CB * 5 * N * N * N + 3 * CB * 5 * QC * QC * QC) * sizeof(double) + 64;
   if (smem > 227 * 1024) return -2;
   auto k = dg_ekgrad_kernel<N, QC, QV, CB, GEO>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   k<<<(kp.Nc + CB - 1) / CB, NT, smem, st>>>(kp, U, G, inv_volume);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -723,11 +717,8 @@ int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, v
   auto k = dg_op_kernel<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>;
   constexpr size_t smem = op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
   if (smem > 227 * 1024) return -2;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   const int grid = (kp.Nc + CB - 1) / CB;
   k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout),
                                           static_cast<T*>(dU), Uout);
@@ -875,11 +866,8 @@ int launch_op_warp(const KParams& kp, const double* U, const void* Rin, void* Ro
   constexpr size_t smem = warp_smem_bytes<T, N, QC, QV, WPC, CELL, FACE, MASS, GEO>();
   if (smem > 227 * 1024) return -2;
   auto k = dg_op_warp_kernel<T, N, QC, QV, WPC, CELL, FACE, MASS, GEO>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   const int grid = (kp.Nc + WPC - 1) / WPC;
   k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout), static_cast<T*>(dU),
                                     Uout);
@@ -955,11 +943,8 @@ int diag_launch_geo(const KParams& kp, const double* U, const void* LU, double* 
   auto k = dg_diag_kernel<TL, N, QC, QV, CB, GEO>;
   constexpr size_t smem = diag_smem_bytes<N, QC, QV, CB, GEO>();
   if (smem > 227 * 1024) return -2;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    attr = true;
-  }
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
   const int grid = (kp.Nc + CB - 1) / CB;
   *nblocks = grid;
   if (partial == nullptr) return 0;
@@ -1223,11 +1208,8 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     constexpr size_t smem = face_warp_smem_bytes<T, N, QC, QV, WPC, GEO>();
     static_assert(smem <= 227 * 1024, "face kernel shared memory");
     auto k = dg_face_warp_kernel<T, N, QC, QV, WPC, GEO>;
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-      attr = true;
-    }
+    static bool attr[kMaxDevices] = {};
+    if (smem_attr_once(k, smem, attr)) return -1;
     const dim3 grid((kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
     k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<T*>(FB));
   } else {
@@ -1235,11 +1217,8 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     constexpr size_t smem = face_smem_bytes<T, N, QC, QV, CB, GEO>();
     static_assert(smem <= 227 * 1024, "face kernel shared memory");
     auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-      attr = true;
-    }
+    static bool attr[kMaxDevices] = {};
+    if (smem_attr_once(k, smem, attr)) return -1;
     const dim3 grid((kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
     k<<<grid, face_threads<T, GEO>(), smem, st>>>(kp, U, static_cast<T*>(FB));
   }
@@ -1268,6 +1247,8 @@ int faces_dispatch(const KParams& kp, const double* U, void* FB, cudaStream_t st
 // instantiations compile in parallel.
 template <int N, int QC, int QV, int PART>
 void fill_launchers(Launchers& L) {
+  static_assert(PART >= 0 && PART < DGCNS_PARTS && DGCNS_PARTS == 7, "parts");
+  L.const_tables[PART] = upload_const_tables<N, QC, QV>;
   if constexpr (PART == 0) {  // FP64 operator
     L.features = Feat<N, QC, QV>::bits;
     L.op_fp64 = op_dispatch<double, N, QC, QV>;

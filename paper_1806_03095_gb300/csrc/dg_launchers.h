@@ -56,6 +56,9 @@ struct Launchers {
   EkGradFn ekgrad;
   int (*dev_fp32)(const KParams&, const double* U, void* D, cudaStream_t);  // D = float(U - U_ref)
   int cb_fp64, cb_fp32;
+  // per part: write the 1D tables (layout of make_layout, FP64 and FP32) to the part's constant memory on
+  // the current device
+  int (*const_tables[7])(const double* t64, const float* t32, cudaStream_t);
 };
 
 // (N = k+1, QC, QV) triples compiled into the library.  Default rules:

@@ -250,16 +250,21 @@ int launch_mass_tma(const KParams& kp, const void* Rin, void* Rout, void* dU, co
   constexpr size_t smem = mass_tma_bytes<T, N, QC, QV, STAGE>(CB);
   static_assert(smem <= 227 * 1024, "mass kernel shared memory");
   auto k = dg_mass_tma_kernel<T, N, QC, QV, CB, STAGE, GEO>;
-  static int grid_per_sm = 0;
-  static int nsm = 0;
+  // persistent grid: SMs x resident CTAs of the current device (looked up once per device)
+  static int grid_per_sm_dev[kMaxDevices] = {};
+  static int nsm_dev[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+  int& grid_per_sm = grid_per_sm_dev[dev];
+  int& nsm = nsm_dev[dev];
   if (grid_per_sm == 0) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, k, kMassThreads, smem) != cudaSuccess ||
-        grid_per_sm < 1)
+    int g = 0, m = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k, kMassThreads, smem) != cudaSuccess || g < 1)
       return -1;
+    nsm = m;
+    grid_per_sm = g;
   }
   const int nbatch = (kp.Nc + CB - 1) / CB;
   const int grid = nbatch < nsm * grid_per_sm ? nbatch : nsm * grid_per_sm;

@@ -250,6 +250,7 @@ const Registry kRegistry[] = {DGCNS_CONFIGS(DGCNS_ENTRY)};
 struct dgcns_ctx {
   dgcns_mesh mesh;
   dgcns_params prm;
+  int device = 0;  // the CUDA device current at dg_cns_create: every call runs there
   cudaStream_t stream = nullptr;
   Launchers L{};
   KParams kp{};
@@ -287,6 +288,21 @@ struct dgcns_ctx {
 
 static thread_local std::string g_create_err = "no error";
 
+// Every entry point runs on its context's device: it makes that device current for the call and
+// gives the caller's current device back on return.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(const dgcns_ctx* c) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != c->device && cudaSetDevice(c->device) == cudaSuccess) prev = cur;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 static int fail(dgcns_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -311,6 +327,15 @@ static int create_fail(dgcns_ctx* c, const char* what) {
 static size_t res_bytes(const dgcns_ctx* c) {
   return c->state_elems * (c->prm.precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
 }
+
+// Arrays given to one call must not share memory (views at an offset included): [a, a + na) and
+// [b, b + nb) in bytes.
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+static size_t state_bytes(const dgcns_ctx* c) { return c->state_elems * sizeof(double); }
 
 static void map_point(const dgcns_mesh& m, double* x) {
   const double L[3] = {m.hi[0] - m.lo[0], m.hi[1] - m.lo[1], m.hi[2] - m.lo[2]};
@@ -536,6 +561,7 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     tau[e] = c->nu * (k + 1) * (k + 1) * a / vol;
   }
 
+  if (cudaGetDevice(&c->device) != cudaSuccess) return create_fail(c, "cudaGetDevice");
   if (cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->d_tau, tau.size() * sizeof(double)) != cudaSuccess)
@@ -544,6 +570,11 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
       cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return create_fail(c, "table upload");
+  // the 1D operators also go to the constant memory of every part (the same values for every context of
+  // this (k, nq_conv, nq_visc), so rewriting them is harmless to contexts already running)
+  for (int q = 0; q < DGCNS_PARTS; ++q)
+    if (c->L.const_tables[q] && c->L.const_tables[q](t64.data(), t32.data(), c->stream) != 0)
+      return create_fail(c, "constant tables");
   const size_t fb_bytes = (size_t)c->Nc * 60 * N * N * (prm->precision == DGCNS_MIXED ? sizeof(float) : sizeof(double));
   if (cudaMalloc(&c->d_R, res_bytes(c)) != cudaSuccess ||
       (prm->precision == DGCNS_MIXED && cudaMalloc(&c->d_dev, c->state_elems * sizeof(float)) != cudaSuccess) ||
@@ -684,6 +715,7 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
 
 int dg_cns_destroy(dgcns_ctx* c) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaFree(c->d_tab64);
   cudaFree(c->d_tab32);
@@ -746,6 +778,7 @@ static int with_device_coords(dgcns_ctx* c, const std::function<void(const doubl
 
 int dg_cns_set_initial_tgv(dgcns_ctx* c, double* U) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U) return fail(c, DGCNS_ERR_INVALID_ARG, "U is NULL");
   const dgcns_params& p = c->prm;
   const double U0 = p.U0, c0 = U0 / p.Ma, T0 = c0 * c0 / (p.gamma * p.R), p0 = p.rho0 * p.R * T0;
@@ -758,6 +791,7 @@ int dg_cns_set_initial_tgv(dgcns_ctx* c, double* U) {
 
 int dg_cns_set_initial_channel(dgcns_ctx* c, double* U, uint64_t seed) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U) return fail(c, DGCNS_ERR_INVALID_ARG, "U is NULL");
   const dgcns_params& p = c->prm;
   if (!(p.u_mach > 0.0)) return fail(c, DGCNS_ERR_INVALID_ARG, "the channel start needs u_mach (u_max) > 0");
@@ -770,6 +804,7 @@ int dg_cns_set_initial_channel(dgcns_ctx* c, double* U, uint64_t seed) {
 
 int dg_cns_node_coords(dgcns_ctx* c, double* xyz) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!xyz) return fail(c, DGCNS_ERR_INVALID_ARG, "xyz is NULL");
   const std::vector<double> host = host_node_coords(c->mesh, c->prm.k);
   if (cudaMemcpyAsync(xyz, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
@@ -895,8 +930,9 @@ static int eval_L(dgcns_ctx* c, KParams kp, const double* U, void* dst, void* dU
 
 int dg_cns_apply(dgcns_ctx* c, const double* U, void* R, int op) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U || !R) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
-  if ((const void*)U == R) return fail(c, DGCNS_ERR_INVALID_ARG, "R must not alias U");
+  if (overlap(U, state_bytes(c), R, res_bytes(c))) return fail(c, DGCNS_ERR_INVALID_ARG, "R must not overlap U");
   KParams kp = c->kp;
   switch (op) {
     case DGCNS_OP_L:
@@ -927,6 +963,7 @@ int dg_cns_apply(dgcns_ctx* c, const double* U, void* R, int op) {
 
 int dg_cns_inverse_mass(dgcns_ctx* c, const void* in, void* out) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!in || !out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   KParams kp = c->kp;
   kp.out_mode = 0;
@@ -936,10 +973,14 @@ int dg_cns_inverse_mass(dgcns_ctx* c, const void* in, void* out) {
 
 int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* U_in, void* dU, double* U_out) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   (void)t;  // the operator is autonomous (constant body force)
   if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
   if (!U_in || !dU || !U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
-  if (dU == (const void*)U_in || dU == (const void*)U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "dU must not alias U_in or U_out");
+  if (overlap(dU, res_bytes(c), U_in, state_bytes(c)) || overlap(dU, res_bytes(c), U_out, state_bytes(c)))
+    return fail(c, DGCNS_ERR_INVALID_ARG, "dU must not overlap U_in or U_out");
+  if (U_in != U_out && overlap(U_in, state_bytes(c), U_out, state_bytes(c)))
+    return fail(c, DGCNS_ERR_INVALID_ARG, "U_out must be U_in itself or not overlap it");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
   if (c->prm.kernel == DGCNS_KERNEL_FUSED && U_in == U_out)
     return fail(c, DGCNS_ERR_INVALID_ARG, "fused kernel needs U_out != U_in");
@@ -953,9 +994,11 @@ int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* 
 
 int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (nsteps < 0) return fail(c, DGCNS_ERR_INVALID_ARG, "nsteps < 0");
-  if (!U || !U_tmp || !dU || U == U_tmp || dU == (const void*)U || dU == (const void*)U_tmp)
-    return fail(c, DGCNS_ERR_INVALID_ARG, "U, U_tmp and dU must be distinct non-NULL arrays");
+  if (!U || !U_tmp || !dU || overlap(U, state_bytes(c), U_tmp, state_bytes(c)) ||
+      overlap(dU, res_bytes(c), U, state_bytes(c)) || overlap(dU, res_bytes(c), U_tmp, state_bytes(c)))
+    return fail(c, DGCNS_ERR_INVALID_ARG, "U, U_tmp and dU must be non-NULL arrays that do not overlap");
   double* a = U;
   double* b = U_tmp;
   // Mixed form (fused or face-centric kernels): the stage kernel also writes float(U_out - U_ref)
@@ -1017,10 +1060,11 @@ static int run_adj(dgcns_ctx* c, KParams ka, const double* U, void* G, double* l
 
 int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U || !W || !G) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
   if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
-  if (G == (const void*)U) return fail(c, DGCNS_ERR_INVALID_ARG, "G must not alias U");
+  if (overlap(G, res_bytes(c), U, state_bytes(c))) return fail(c, DGCNS_ERR_INVALID_ARG, "G must not overlap U");
   KParams km = c->kp;
   km.out_mode = 0;
   km.has_bf = 0;
@@ -1033,12 +1077,15 @@ int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) 
 
 int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_in, double* lam_U, void* lam_dU) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
   if (!U_in || !lam_U || !lam_dU) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
   if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
-  if ((const void*)lam_U == (const void*)U_in) return fail(c, DGCNS_ERR_INVALID_ARG, "lam_U must not alias U_in");
+  if (overlap(lam_U, state_bytes(c), U_in, state_bytes(c)) || overlap(lam_dU, res_bytes(c), U_in, state_bytes(c)) ||
+      overlap(lam_dU, res_bytes(c), lam_U, state_bytes(c)))
+    return fail(c, DGCNS_ERR_INVALID_ARG, "U_in, lam_U and lam_dU must not overlap");
   const PrepFn prep = c->prm.precision == DGCNS_MIXED ? c->L.prep_fp32 : c->L.prep_fp64;
   // W = lam_dU + B lam_U (scratch), lam_dU <- A W
   {
@@ -1060,7 +1107,9 @@ int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_
 
 int dg_cns_kinetic_energy_gradient(dgcns_ctx* c, const double* U, double* G) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
-  if (!U || !G || (const void*)U == (const void*)G) return fail(c, DGCNS_ERR_INVALID_ARG, "bad arrays");
+  DeviceScope ds(c);
+  if (!U || !G || overlap(U, state_bytes(c), G, state_bytes(c)))
+    return fail(c, DGCNS_ERR_INVALID_ARG, "U and G must be non-NULL arrays that do not overlap");
   KParams kp = c->kp;
   kp.tables = c->d_tab64;
   if (c->g64[0]) {
@@ -1090,6 +1139,7 @@ static KParams diag_params(const dgcns_ctx* c) {
 
 int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* out) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U || !out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   KParams kp = diag_params(c);
   int nblk = 0;
@@ -1146,15 +1196,18 @@ int noalloc_scratch(dgcns_ctx* c, double** out) {
   return DGCNS_OK;
 }
 
-// Sum the partial rows in order (the same order as the host reduction of
-// dg_cns_diagnostics) and write the normalised diagnostics.
+// Sum the partial rows and write the normalised diagnostics: warp w sums column w (lane l takes rows
+// l, l + 32, ... in order, then a shuffle tree in a fixed order), so the result is deterministic and
+// differs from the host's serial sum only by rounding.
 __global__ void noalloc_finalize(const double* __restrict__ partial, int nrows, double nu, int has_L,
                                  double* __restrict__ out) {
   __shared__ double acc[10];
-  if (threadIdx.x < 10) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 10) {
     double s = 0.0;
-    for (int b = 0; b < nrows; ++b) s += partial[(size_t)b * 10 + threadIdx.x];
-    acc[threadIdx.x] = s;
+    for (int b = lane; b < nrows; b += 32) s += partial[(size_t)b * 10 + w];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) acc[w] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1171,6 +1224,7 @@ extern "C" {
 
 int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, double* out_dev) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (!U || !out_dev) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   KParams kp = diag_params(c);
   const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
@@ -1184,7 +1238,7 @@ int dg_cns_diagnostics_noalloc(dgcns_ctx* c, const double* U, const void* LU, do
   const int r = noalloc_scratch(c, &scratch);
   if (r) return r;
   if (f(kp, U, LU, scratch, &nblk, c->stream) != 0) return cuda_fail(c, "no-alloc diagnostics kernel launch");
-  noalloc_finalize<<<1, 32, 0, c->stream>>>(scratch, nblk, c->nu, LU ? 1 : 0, out_dev);
+  noalloc_finalize<<<1, 320, 0, c->stream>>>(scratch, nblk, c->nu, LU ? 1 : 0, out_dev);
   c->launches += 2;
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, "no-alloc diagnostics finalize launch");
   return DGCNS_OK;
@@ -1198,6 +1252,7 @@ int dg_cns_launch_count(const dgcns_ctx* c, int64_t* count) {
 
 int dg_cns_status(dgcns_ctx* c) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   int h = 0;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
       cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1211,6 +1266,7 @@ int dg_cns_status(dgcns_ctx* c) {
 
 int dg_cns_timing(dgcns_ctx* c, int enable) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   const int r = flush_times(c);
   if (r) return r;
   if (enable) {
@@ -1225,6 +1281,7 @@ int dg_cns_timing(dgcns_ctx* c, int enable) {
 
 int dg_cns_kernel_times(dgcns_ctx* c, double* ms, int64_t* counts, int n) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
   if (n < 0 || n > DGCNS_KT_COUNT) return fail(c, DGCNS_ERR_INVALID_ARG, "n must be 0..DGCNS_KT_COUNT");
   const int r = flush_times(c);
   if (r) return r;

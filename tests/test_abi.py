@@ -90,13 +90,13 @@ def _no_device():
 
 @pytest.mark.skipif(not _no_device(), reason="the failure path of a machine without a GPU")
 def test_create_without_a_device_reports_the_cuda_error(lib):
-    """A valid configuration on a machine without a GPU: the first device allocation fails, the call
+    """A valid configuration on a machine without a GPU: the first CUDA call (the device lookup) fails, the call
     returns DGCNS_ERR_CUDA (not OOM) with the CUDA error in the message, and no context."""
     m, p = _mesh_params(3, 5, 4)
     ctx = ctypes.c_void_p()
     assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -3
     assert ctx.value is None
-    assert lib.dg_cns_last_error(None).startswith(b"CUDA error (tables): ")
+    assert lib.dg_cns_last_error(None).startswith(b"CUDA error (cudaGetDevice): ")
     # a later failure of a different kind replaces the message
     m.n[0] = 0
     assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -1

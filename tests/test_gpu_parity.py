@@ -483,3 +483,25 @@ def test_geometry_on_the_fly_unsupported_and_invalid():
     with pytest.raises(api.DGCNSError) as ei:
         pair_mapped((2, 2, 2), 3, 2, 0.05, (1, 1, 1), (-PI,) * 3, (PI,) * 3, geometry=7)
     assert ei.value.code == -1
+
+
+def test_overlapping_arrays_are_rejected_before_any_launch():
+    """Arrays of one call must not share memory: views at an offset inside another argument are refused with
+    INVALID_ARG before anything runs; adjacent non-overlapping ranges of one buffer are accepted."""
+    import ctypes
+    g, op = pair((2, 2, 2), 2, kernel=2)
+    U = on_gpu(inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 18))
+    n = U.numel()
+    buf = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    buf[:n] = U.reshape(-1)
+    p = lambda off: ctypes.c_void_p(buf.data_ptr() + 8 * off)  # noqa: E731
+    lib = g.lib
+    assert lib.dg_cns_apply(g.ctx, p(0), p(8), api.OP_L) == -1
+    assert b"overlap" in lib.dg_cns_last_error(g.ctx)
+    assert lib.dg_cns_rk_stage(g.ctx, 1, 1e-3, 0.0, p(0), p(n - 8), p(2 * n)) == -1
+    assert lib.dg_cns_rk_stage(g.ctx, 1, 1e-3, 0.0, p(0), p(2 * n), p(8)) == -1
+    assert lib.dg_cns_rk_steps(g.ctx, 1, 1e-3, 0.0, p(0), p(n // 2), p(2 * n)) == -1
+    assert lib.dg_cns_adjoint_apply(g.ctx, p(0), p(n), p(n - 1)) == -1
+    assert lib.dg_cns_apply(g.ctx, p(0), p(n), api.OP_L) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(buf[n:2 * n].reshape(U.shape), g.apply(U))

@@ -40,12 +40,14 @@ def test_noalloc_diagnostics_match_two_calls_in_a_row(precision):
         assert rc == 0, lib.dg_cns_last_error(g.ctx)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), (got, ref)
+        # the GPU sums the partial rows in another order than the host: the integrals of momentum (about 0
+        # on this periodic box) agree to rounding in absolute terms
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12), (got, ref)
     # without L(U): -de_k/dt is reported as 0, the rest unchanged
     out2 = g.dg_cns_diagnostics_noalloc(U)
     torch.cuda.synchronize()
     ref2 = g.diagnostics(U)
-    assert np.allclose(out2.cpu().numpy(), ref2, rtol=1e-12, atol=1e-15)
+    assert np.allclose(out2.cpu().numpy(), ref2, rtol=1e-12, atol=1e-12)
 
 
 def test_noalloc_rejects_mesh_beyond_scratch():
