@@ -366,8 +366,7 @@ def extras(args, cfg):
                                   "rel_max": float(d.abs().max() / L64.abs().max())}
     del g64, g32, U, L64, L32, d
     torch.cuda.empty_cache()
-    res["adjoint"] = adjoint_cost(kernel=2)
-    res["adjoint_element_centric"] = adjoint_cost(kernel=1)
+    res["adjoint"], res["adjoint_element_centric"], res["adjoint_mixed"] = adjoint_extras()
     res.update(other_workloads(steps))
     res["mixed_dissipation_history"] = dissipation_history()
     res["memory_bound_kernels"] = memory_bound_kernels()
@@ -567,46 +566,85 @@ def dissipation_history(t_final=2.0, every=8):
     return out
 
 
-def adjoint_cost(nsteps=200, every=20, kernel=2):
-    """Discrete adjoint of TGV 24^3, k = 4 (FP64): forward nsteps RK(5,4) steps with a checkpoint every `every`
-    steps, then the gradient of the final kinetic energy with respect to the initial velocity field (recomputation
-    of the segments + stage adjoints).  Reports forward and gradient times and their ratio.  kernel 2: face-centric
-    forward and adjoint kernels; kernel 1: element-centric (fused forward, element-centric adjoint kernel)."""
+def adjoint_cost(nsteps=200, every=20, kernel=2, fd_dirs=0, precision=0):
+    """Discrete adjoint of TGV 24^3, k = 4: forward nsteps RK(5,4) steps with a checkpoint every `every` steps,
+    then the gradient of the final kinetic energy with respect to the initial velocity field (recomputation of
+    the segments + stage adjoints).  Reports forward and gradient times and their ratio.  kernel 2: face-centric
+    forward and adjoint kernels; kernel 1: element-centric (fused forward, element-centric adjoint kernel).
+    fd_dirs > 0 (FP64): central differences of the forward integration (step 1e-6) along that many seeded
+    directions (inputs.fd_direction) against the adjoint's directional derivatives.  Returns (report, gradient)."""
     from paper_1806_03095_gb300 import adjoint as adj, configs, inputs
-    cfg = configs.WORKLOADS["tgv24_k4"](precision=0, kernel=kernel)
+    cfg = configs.WORKLOADS["tgv24_k4"](precision=precision, kernel=kernel)
     g = configs.make_context(cfg)
-    U0 = inputs.tgv_state(g.node_coords())
+    xyz = g.node_coords()
+    U0 = inputs.tgv_state(xyz)
     rho = U0[:, 0].clone()
     u0 = (U0[:, 1:4] / rho[:, None]).clone().requires_grad_(True)
     cv = cfg["R"] / (cfg["gamma"] - 1.0)
     T0 = (1.0 / cfg["Ma"]) ** 2 / (cfg["gamma"] * cfg["R"])
     dt = configs.time_step(cfg)
+
+    def state(u):
+        return torch.cat([rho[:, None], rho[:, None] * u, (rho * (cv * T0 + 0.5 * (u * u).sum(1)))[:, None]], 1)
+
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ev[0].record()
-    Ui = torch.cat([rho[:, None], rho[:, None] * u0, (rho * (cv * T0 + 0.5 * (u0 * u0).sum(1)))[:, None]], 1)
-    J = adj.kinetic_energy(g, adj.integrate(g, Ui.contiguous(), nsteps, dt, every))
+    J = adj.kinetic_energy(g, adj.integrate(g, state(u0).contiguous(), nsteps, dt, every))
     ev[1].record()
     J.backward()
     ev[2].record()
     torch.cuda.synchronize()
     fwd = ev[0].elapsed_time(ev[1])
     bwd = ev[1].elapsed_time(ev[2])
-    return {"workload": "TGV 24^3, k=4, FP64, %d RK(5,4) steps, checkpoint every %d, %s kernels"
-            % (nsteps, every, "face-centric" if kernel == 2 else "element-centric"),
-            "forward_ms": round(fwd, 1), "gradient_ms": round(bwd, 1), "gradient_over_forward": round(bwd / fwd, 3),
-            "grad_norm": float(torch.linalg.norm(u0.grad)), "e_k_final": float(J.detach())}
+    grad = u0.grad.detach().clone()
+    out = {"workload": "TGV 24^3, k=4, %s, %d RK(5,4) steps, checkpoint every %d, %s kernels"
+           % ("FP64" if precision == 0 else "mixed", nsteps, every, "face-centric" if kernel == 2 else "element-centric"),
+           "forward_ms": round(fwd, 1), "gradient_ms": round(bwd, 1), "gradient_over_forward": round(bwd / fwd, 3),
+           "grad_norm": float(torch.linalg.norm(grad)), "e_k_final": float(J.detach())}
+    if fd_dirs:
+        h = 1e-6
+        u = u0.detach()
+
+        def J_of(uu):
+            return float(g.diagnostics(g.rk_steps(nsteps, dt, 0.0, state(uu).contiguous()))[0])
+
+        checks = []
+        for i in range(fd_dirs):
+            v = inputs.fd_direction(u, xyz, 1806 + i).to(u.device)
+            dJ = float((grad * v).sum())
+            fd = (J_of(u + h * v) - J_of(u - h * v)) / (2 * h)
+            checks.append({"direction": i, "adjoint": dJ, "central_difference": fd, "rel_err": abs(dJ - fd) / abs(fd)})
+        out["fd_check"] = {"step": h, "directions": "inputs.fd_direction seeds 1806.., unit RMS", "results": checks,
+                           "max_rel_err": max(c["rel_err"] for c in checks)}
+    del g
+    torch.cuda.empty_cache()
+    return out, grad
+
+
+def adjoint_extras():
+    """The adjoint workload in FP64 (cost, and central differences along 2 directions), element-centric, and in
+    the mixed form with its gradient's error against the FP64 gradient."""
+    fp64, g64 = adjoint_cost(kernel=2, fd_dirs=2)
+    ec, _ = adjoint_cost(kernel=1)
+    mixed, g32 = adjoint_cost(kernel=2, precision=1)
+    d = g32 - g64
+    mixed["gradient_error_vs_fp64"] = {"rel_l2": float(torch.linalg.norm(d) / torch.linalg.norm(g64)),
+                                       "rel_max": float(d.abs().max() / g64.abs().max())}
+    return fp64, ec, mixed
 
 
 # -- CPU oracle --------------------------------------------------------------------------------------
-def oracle_sample(cfg, target_s=12.0):
-    """Time the FP64 oracle's L(U) on a bounded sample of the workload: a 16^3-cell periodic TGV mesh with the
-    workload's k and quadrature (same per-node work), repeated until ~target_s seconds of CPU time."""
+def oracle_sample(cfg, target_s=12.0, n=None):
+    """Time the FP64 oracle's L(U) on a bounded sample of the workload: an n^3-cell periodic TGV mesh (default
+    16^3, 8^3 above k = 3) with the workload's k and quadrature (same per-node work), repeated until ~target_s
+    seconds, on torch's current CPU thread count."""
     from oracle import physics as ph
     from oracle.mesh import BoxMesh
     from oracle.operator import DGOperator
     from paper_1806_03095_gb300 import inputs
-    n = 16 if cfg["k"] <= 3 else 8
+    if n is None:
+        n = 16 if cfg["k"] <= 3 else 8
     mesh = BoxMesh((n, n, n), cfg["lo"], cfg["hi"], cfg["periodic"], cfg["k"])
     phys = ph.Physics.from_numbers(cfg["Re"], cfg["Pr"], cfg["Ma"], cfg["gamma"], cfg["R"])
     op = DGOperator(mesh, phys, cfg["nq_conv"], cfg["nq_visc"])
@@ -625,8 +663,50 @@ def oracle_sample(cfg, target_s=12.0):
             "periodic TGV mesh, k=%d, %d evaluations in %.1f s" % (n, cfg["k"], reps, el), "seconds": round(el, 2)}
 
 
+def oracle_rk_steps(max_steps=10, budget_s=20.0):
+    """The oracle's RK(5,4) steps on the Taylor-Green vortex 8^3, k = 3 (the small parity workload): up to
+    max_steps steps, stopping once budget_s seconds have passed; GDoF/s per stage."""
+    from oracle import physics as ph, rk as ork
+    from oracle.mesh import BoxMesh
+    from oracle.operator import DGOperator
+    from paper_1806_03095_gb300 import configs, inputs
+    cfg = configs.tgv(8, 3)
+    mesh = BoxMesh(cfg["ncells"], cfg["lo"], cfg["hi"], cfg["periodic"], cfg["k"])
+    op = DGOperator(mesh, ph.Physics.from_numbers(cfg["Re"], cfg["Pr"], cfg["Ma"], cfg["gamma"], cfg["R"]),
+                    cfg["nq_conv"], cfg["nq_visc"])
+    U = inputs.tgv_state(op.xyz)
+    dt = configs.time_step(cfg)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        U = ork.step(lambda V, t: op.L(V), U, dt, steps * dt)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    dofs = 5 * mesh.Nc * mesh.n ** 3
+    return {"value": round(dofs * ork.STAGES * steps / el / 1e9, 6), "unit": UNIT, "cores": torch.get_num_threads(),
+            "sample": "%d RK(5,4) steps of the oracle on TGV 8^3, k=3 in %.1f s" % (steps, el), "steps": steps}
+
+
 def cpu_baseline(cfg):
-    return oracle_sample(cfg)
+    """The naive FP64 oracle on the host cores, a reported baseline (not the target): L(U) on a bounded sample
+    with every core (nproc), the same on one core, and RK(5,4) steps on TGV 8^3, k = 3."""
+    threads = torch.get_num_threads()
+    nproc = os.cpu_count() or 1
+    try:
+        torch.set_num_threads(nproc)
+        out = oracle_sample(cfg)
+        torch.set_num_threads(1)
+        out["single_core"] = oracle_sample(cfg, target_s=8.0, n=8 if cfg["k"] <= 3 else 4)
+        torch.set_num_threads(nproc)
+        out["rk_steps_tgv8_k3"] = oracle_rk_steps()
+    finally:
+        torch.set_num_threads(threads)
+    out["nproc"] = nproc
+    out["label"] = "naive FP64 oracle: a reported baseline, not the target"
+    out["paper_context"] = ("the paper's node: 0.33 GDoF/s per stage at k=3 with the 3/2 rule on 28 Haswell cores "
+                            "(FP64, PID table; context, not the target)")
+    return out
 
 
 def reference_arm(args, ws, rank):

@@ -125,6 +125,16 @@ def smooth_direction(xyz, seed, kmax=1):
     return v / torch.sqrt((v * v).mean())
 
 
+def fd_direction(u0, xyz, seed):
+    """Seeded direction for central differences of a functional of the velocity field u0 [Nc, 3, n^3]: the
+    field itself (scaled to unit root-mean-square) plus smooth_direction(xyz, seed), the sum scaled to unit
+    root-mean-square.  Its directional derivative stays well above the rounding noise of the differences,
+    which a purely random direction (nearly orthogonal to the gradient) does not guarantee."""
+    u = u0.double().cpu()
+    v = u / torch.sqrt((u * u).mean()) + smooth_direction(xyz, seed)
+    return v / torch.sqrt((v * v).mean())
+
+
 def random_direction(shape, seed):
     """Seeded standard-normal array normalised to unit 2-norm (adjoint test directions)."""
     v = torch.randn(tuple(shape), generator=_gen(seed), dtype=torch.float64)

@@ -389,9 +389,12 @@ def test_adjoint_workload_gradient_vs_central_differences():
     """The adjoint workload: TGV 24^3, k = 4, 200 RK(5,4) steps with checkpoints every 20 steps; the gradient
     of the final kinetic energy with respect to the initial nodal velocity field (discrete adjoint through
     torch.autograd.Function) against central differences of the CUDA forward integration along 8 seeded
-    smooth directions of unit root-mean-square, step 1e-6, in FP64: 1e-6 relative to each directional
-    derivative.  The state is the smooth Taylor--Green field, whose traces differ across faces only by the
-    interpolation error, so a crossing of the LLF max() moves the differences by far less than that."""
+    directions of unit root-mean-square (inputs.fd_direction: the initial field plus a smooth random field),
+    step 1e-6, in FP64: 1e-6 relative to each directional derivative.  Two 200-step trajectories differ by
+    rounding noise of about 3e-10 in the central difference, so the directions keep the derivative O(1);
+    with purely random smooth directions one of 8 had a derivative of 2e-4 and missed the bound by that
+    noise (1.4e-6).  The state is the smooth Taylor--Green field, whose traces differ across faces only by
+    the interpolation error, so a crossing of the LLF max() moves the differences by far less than that."""
     from paper_1806_03095_gb300 import adjoint as adj
     cfg, g = full_size("tgv24_k4", 0)
     dt, nsteps, every, h = configs.time_step(cfg), 200, 20, 1e-6
@@ -411,8 +414,10 @@ def test_adjoint_workload_gradient_vs_central_differences():
         U = g.rk_steps(nsteps, dt, 0.0, control_to_state(u, rho, T0, cv).contiguous())
         return float(g.diagnostics(U)[0])
 
+    res = []
     for i in range(8):
-        v = inputs.smooth_direction(xyz, 1806 + i).to(grad.device)
+        v = inputs.fd_direction(u0, xyz, 1806 + i).to(grad.device)
         dJ = float((grad * v).sum())
         fd = (J_fd(u0 + h * v) - J_fd(u0 - h * v)) / (2 * h)
-        assert abs(dJ - fd) <= TOL_FD * abs(fd), (i, dJ, fd)
+        res.append((i, dJ, fd, abs(dJ - fd) / abs(fd)))
+    assert all(r[3] <= TOL_FD for r in res), res
