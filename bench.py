@@ -207,6 +207,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
     ap.add_argument("--inverse-mass", action="store_true",
                     help="time dg_cns_inverse_mass alone on the workload (one JSON line; not the step metric)")
+    ap.add_argument("--stability", action="store_true",
+                    help="critical Cr (and with --with-d D) numbers of the TGV, the paper's time-step study")
+    ap.add_argument("--schemes", default="lsrk54,lsrk33")
+    ap.add_argument("--degrees", default="3")
+    ap.add_argument("--with-d", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_init(args)
@@ -214,6 +219,8 @@ def main():
         return reference_arm(args, ws, rank)
     if args.inverse_mass:
         return inverse_mass_only(args)
+    if args.stability:
+        return stability(args)
 
     from paper_1806_03095_gb300 import configs, roofline
     device = local if torch.cuda.is_available() else None
@@ -455,6 +462,78 @@ def memory_bound_kernels(reps=20):
         del g, R, Y, ctx, bufs
         torch.cuda.empty_cache()
     return out
+
+
+def stability_run(cfg, scheme, number, which, t_final, chunk=50):
+    """Integrate the Taylor-Green vortex with the 2N scheme to t_final at Courant number `number` (which = "Cr")
+    or viscous number (which = "D", the other restriction made slack); unstable when the state turns
+    non-finite or the kinetic energy exceeds twice its initial value.  Returns (stable, steps, t reached)."""
+    from paper_1806_03095_gb300 import api, configs, inputs, schemes
+    g = configs.make_context(cfg)
+    U = inputs.tgv_state(g.node_coords()).contiguous()
+    Ut, dU = g.empty_state(), g.empty_residual()
+    nu = 1.0 / cfg["Re"]
+    if which == "Cr":
+        dt = api.cfl_dt(cfg["k"], cfg["h_min"], cfg["u_max"], cfg["Ma"], Cr=number, D=1e9, nu=nu)
+    else:
+        dt = api.cfl_dt(cfg["k"], cfg["h_min"], cfg["u_max"], cfg["Ma"], Cr=1e9, D=number, nu=nu)
+    nsteps = int(math.ceil(t_final / dt))
+    ek0 = float(g.diagnostics(U)[0])
+    done = 0
+    while done < nsteps:
+        n = min(chunk, nsteps - done)
+        g.lsrk_steps(schemes.SCHEMES[scheme], n, dt, U, Ut, dU)
+        done += n
+        d = g.diagnostics(U, check=False)
+        if not (d[8] == 0 and math.isfinite(float(d[0])) and float(d[0]) <= 2.0 * ek0):
+            del g
+            return False, done, done * dt
+    del g
+    return True, done, done * dt
+
+
+def stability(args):
+    """The paper's time-step study (Sec. 4.2.2, critical Cr and D numbers with e = 1.5, f = 3): Taylor-Green
+    vortex at effective resolution 60^3 or 64^3 (k = 2, 3, 5 on 20^3, 16^3, 10^3 cells), Re = 1600 to t = 20
+    for Cr, Re = 1 to t = 1 for D; bisection to 0.02 between a stable and an unstable number, for each 2N
+    scheme of schemes.SCHEMES named in --schemes.  FP64, face-centric kernels.  One JSON line."""
+    from paper_1806_03095_gb300 import configs, schemes
+    torch.cuda.set_device(0)
+    cells = {2: 20, 3: 16, 5: 10}
+    out = {"study": "critical Courant and viscous numbers, TGV, e=1.5, f=3 (Sec. 4.2.2)", "results": []}
+    for scheme in args.schemes.split(","):
+        for k in [int(v) for v in args.degrees.split(",")]:
+            # brackets: a number assumed stable (checked) and one assumed unstable (checked)
+            cr_lo = 0.3 if len(schemes.SCHEMES[scheme][0]) >= 5 else 0.14
+            for which, lo, hi, Re, tf in (("Cr", cr_lo, 1.6, 1600.0, 20.0), ("D", 0.02, 0.2, 1.0, 1.0)):
+                if which == "D" and not args.with_d:
+                    continue
+                cfg = dict(configs.tgv(cells[k], k, precision=0, kernel=2), Re=Re)
+                runs = []
+                ok_lo = stability_run(cfg, scheme, lo, which, tf)
+                ok_hi = stability_run(cfg, scheme, hi, which, tf)
+                runs += [(lo, ok_lo[0]), (hi, ok_hi[0])]
+                if not ok_lo[0] or ok_hi[0]:
+                    out["results"].append({"scheme": scheme, "k": k, "which": which, "bracket_failed": runs})
+                    continue
+                step = 0.02 if which == "Cr" else 0.002
+                while hi - lo > step * 1.0001:
+                    mid = round(0.5 * (lo + hi) / step) * step
+                    if mid <= lo or mid >= hi:
+                        mid = lo + step
+                    st = stability_run(cfg, scheme, mid, which, tf)
+                    runs.append((round(mid, 4), st[0]))
+                    if st[0]:
+                        lo = mid
+                    else:
+                        hi = mid
+                out["results"].append({"scheme": scheme, "k": k, "cells": "%d^3" % cells[k], "which": which,
+                                       "stable": round(lo, 4), "unstable": round(hi, 4),
+                                       "per_stage_stable": round(lo / len(schemes.SCHEMES[scheme][0]), 4),
+                                       "runs": runs})
+                print(json.dumps(out["results"][-1]), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def inverse_mass_only(args):

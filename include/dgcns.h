@@ -170,6 +170,23 @@ int dg_cns_rk_stage(dgcns_ctx* ctx, int stage, double dt, double t, const double
  * INVALID_ARG). */
 int dg_cns_rk_steps(dgcns_ctx* ctx, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU);
 
+/* One stage of any 2N-storage explicit Runge--Kutta scheme, with the stage's
+ * coefficients given by the caller (Sec. 2.4: the paper integrates with a
+ * low-storage scheme of this form, the 7-stage third-order scheme of Toulorge
+ * and Desmet, whose coefficients it does not print):
+ *   dU <- A dU + dt L(U_in);  U_out <- U_in + B dU.
+ * Array rules and errors as dg_cns_rk_stage; A and B must be finite
+ * (INVALID_ARG).  dU is read only when A != 0. */
+int dg_cns_lsrk_stage(dgcns_ctx* ctx, double A, double B, double dt, const double* U_in, void* dU, double* U_out);
+
+/* nsteps steps of the 2N scheme with `stages` stages (1..DGCNS_MAX_STAGES)
+ * and coefficients A[stages], B[stages] (HOST arrays, read during the call);
+ * arrays and errors as dg_cns_rk_steps.  dg_cns_rk_steps is this call with the
+ * RK(5,4) coefficients. */
+#define DGCNS_MAX_STAGES 32
+int dg_cns_lsrk_steps(dgcns_ctx* ctx, int stages, const double* A, const double* B, int nsteps, double dt, double* U,
+                      double* U_tmp, void* dU);
+
 /* Adjoint (vector-Jacobian product) of the operator of dg_cns_apply(DGCNS_OP_L):
  *   G = (dL/dU)^T W = -(dF/dU)^T M^-1 W     (M symmetric)
  * evaluated by transposed sum factorization and transposed pointwise flux

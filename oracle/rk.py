@@ -8,9 +8,14 @@ from that publication:
 
     dU <- A_i dU + dt L(U, t + C_i dt);   U <- U + B_i dU,   i = 1..5.
 
-Pinned by tests/test_oracle_rk.py: the Butcher tableau derived from (A, B)
+Pinned by tests/test_oracle_rk_diag.py: the Butcher tableau derived from (A, B)
 satisfies all eight order-<=4 conditions, c_i = sum_j a_ij reproduces C, and
 y' = lambda y shows order 4.
+
+The general 2N stage (any coefficients) is lsrk_step; the second scheme here is
+Williamson's (1980) three-stage third-order 2N scheme, whose rational
+coefficients are typed from that publication (pinned by the four order-<=3
+conditions, its failure of order 4, and y' = lambda y showing order 3).
 """
 from fractions import Fraction
 
@@ -35,6 +40,10 @@ LSRK54_C = (
     Fraction(2006345519317, 3224310063776),
     Fraction(2802321613138, 2924317926251),
 )
+
+LSRK33_A = (Fraction(0), Fraction(-5, 9), Fraction(-153, 128))
+LSRK33_B = (Fraction(1, 3), Fraction(15, 16), Fraction(8, 15))
+LSRK33_C = (Fraction(0), Fraction(1, 3), Fraction(3, 4))
 
 STAGES = 5
 A = tuple(float(a) for a in LSRK54_A)
@@ -69,4 +78,13 @@ def step(Lfun, U, dt, t, dU=None):
     for i in range(STAGES):
         dU = A[i] * dU + dt * Lfun(U, t + C[i] * dt)
         U = U + B[i] * dU
+    return U
+
+
+def lsrk_step(Lfun, U, dt, t, Acoef, Bcoef, Ccoef):
+    """One step of the 2N scheme with stage coefficients (A_i, B_i, C_i) of dU/dt = Lfun(U, t)."""
+    dU = U * 0.0
+    for Ai, Bi, Ci in zip(Acoef, Bcoef, Ccoef):
+        dU = float(Ai) * dU + dt * Lfun(U, t + float(Ci) * dt)
+        U = U + float(Bi) * dU
     return U

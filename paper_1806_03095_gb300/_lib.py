@@ -18,12 +18,14 @@ MAP_AFFINE, MAP_CHANNEL, MAP_SINE = 0, 1, 2
 GEO_STORED, GEO_ON_THE_FLY = 0, 1
 OP_L, OP_F, OP_FC, OP_FV = 0, 1, 2, 3
 NDIAG = 9
+MAX_STAGES = 32  # DGCNS_MAX_STAGES of dg_cns_lsrk_steps
 NOALLOC_SCRATCH_BYTES = 16 << 20  # static device scratch of dg_cns_diagnostics_noalloc
 
 # Every symbol include/dgcns.h declares.
 EXPORTS = ("dg_cns_create", "dg_cns_destroy", "dg_cns_set_stream", "dg_cns_sizes", "dg_cns_node_coords",
            "dg_cns_set_initial_tgv", "dg_cns_set_initial_channel",
-           "dg_cns_apply", "dg_cns_inverse_mass", "dg_cns_rk_stage", "dg_cns_rk_steps", "dg_cns_diagnostics",
+           "dg_cns_apply", "dg_cns_inverse_mass", "dg_cns_rk_stage", "dg_cns_rk_steps", "dg_cns_lsrk_stage",
+           "dg_cns_lsrk_steps", "dg_cns_diagnostics",
            "dg_cns_diagnostics_noalloc", "dg_cns_adjoint_apply", "dg_cns_rk_stage_adjoint",
            "dg_cns_kinetic_energy_gradient", "dg_cns_launch_count", "dg_cns_status", "dg_cns_timing", "dg_cns_kernel_times",
            "dg_cns_last_error")
@@ -73,6 +75,8 @@ def load(path=LIB_PATH):
         "dg_cns_inverse_mass": ([vp, vp, vp], ci),
         "dg_cns_rk_stage": ([vp, ci, cd, cd, vp, vp, vp], ci),
         "dg_cns_rk_steps": ([vp, ci, cd, cd, vp, vp, vp], ci),
+        "dg_cns_lsrk_stage": ([vp, cd, cd, cd, vp, vp, vp], ci),
+        "dg_cns_lsrk_steps": ([vp, ci, dp, dp, ci, cd, vp, vp, vp], ci),
         "dg_cns_diagnostics": ([vp, vp, vp, dp], ci),
         "dg_cns_diagnostics_noalloc": ([vp, vp, vp, vp], ci),
         "dg_cns_adjoint_apply": ([vp, vp, vp, vp], ci),

@@ -136,6 +136,29 @@ class DGCNS:
                                              _ptr(dU)))
         return U
 
+    def dg_cns_lsrk_stage(self, A, B, dt, U_in, dU, U_out):
+        self._state(U_in, "U_in")
+        self._state(U_out, "U_out")
+        self._state(dU, "dU", self.rdtype)
+        self._sync_stream()
+        self._check(self.lib.dg_cns_lsrk_stage(self.ctx, float(A), float(B), float(dt), _ptr(U_in), _ptr(dU),
+                                               _ptr(U_out)))
+
+    def dg_cns_lsrk_steps(self, scheme, nsteps, dt, U, U_tmp=None, dU=None):
+        """nsteps steps of a 2N scheme: scheme = (A, B) sequences of stage coefficients (see schemes.py)."""
+        A, B = scheme
+        if len(A) != len(B) or not 1 <= len(A) <= _lib.MAX_STAGES:
+            raise ValueError("a 2N scheme needs equal-length A and B with 1..%d stages" % _lib.MAX_STAGES)
+        self._state(U, "U")
+        U_tmp = self.empty_state() if U_tmp is None else self._state(U_tmp, "U_tmp")
+        dU = self.empty_residual() if dU is None else self._state(dU, "dU", self.rdtype)
+        a = (ctypes.c_double * len(A))(*[float(x) for x in A])
+        b = (ctypes.c_double * len(B))(*[float(x) for x in B])
+        self._sync_stream()
+        self._check(self.lib.dg_cns_lsrk_steps(self.ctx, len(A), a, b, int(nsteps), float(dt), _ptr(U), _ptr(U_tmp),
+                                               _ptr(dU)))
+        return U
+
     def dg_cns_diagnostics(self, U, LU=None, check=True):
         """Returns a float64 numpy array [e_k, eps, -de_k/dt, mass, mom x3, energy, nonfinite]."""
         self._state(U, "U")
@@ -246,6 +269,8 @@ class DGCNS:
     inverse_mass = dg_cns_inverse_mass
     rk_stage = dg_cns_rk_stage
     rk_steps = dg_cns_rk_steps
+    lsrk_stage = dg_cns_lsrk_stage
+    lsrk_steps = dg_cns_lsrk_steps
     diagnostics = dg_cns_diagnostics
     adjoint_apply = dg_cns_adjoint_apply
     rk_stage_adjoint = dg_cns_rk_stage_adjoint

@@ -71,12 +71,15 @@ struct Tab {
   const T *wc, *wv, *wm, *dl0, *dl1;
 };
 
-// The same tables in constant memory, one copy per instantiation (and translation unit), written by
-// upload_const_tables when a context is created.  The sweeps index the 1D operators only with
+// The same tables in constant memory (used by the FP32 kernels), one copy per instantiation and
+// translation unit, written by upload_const_tables when a context is created.  Both have internal linkage (anonymous namespace): as
+// templates with external linkage the linker would merge them across the translation units, and the
+// upload would reach one module's copy only.  The sweeps index the 1D operators only with
 // compile-time offsets, so the FMAs take the coefficients as constant-bank operands: no load
 // instruction per coefficient (from shared memory that was one load per FMA, which bound the FP32
 // kernels by the shared-memory pipe).  Point weights and trace derivatives are indexed per lane and
 // stay in shared memory (the constant cache serialises lane-dependent addresses).
+namespace {
 template <typename T, int N, int QC, int QV>
 __constant__ T c_tab[make_layout(N, QC, QV).total];
 
@@ -90,12 +93,16 @@ int upload_const_tables(const double* t64, const float* t32, cudaStream_t st) {
     return -1;
   return cudaStreamSynchronize(st) == cudaSuccess ? 0 : -1;
 }
+}  // namespace
 
 template <typename T, int N, int QC, int QV>
 __device__ __forceinline__ Tab<T> load_tables(const T* __restrict__ g, T* s) {
   constexpr TableLayout L = make_layout(N, QC, QV);
   for (int i = threadIdx.x; i < L.total; i += blockDim.x) s[i] = g[i];
-  const T* c = c_tab<T, N, QC, QV>;
+  // FP32: operators from constant memory (6 % faster, measured); FP64: from shared memory (the constant
+  // operands made both FP64 kernels 2-3 % slower, measured)
+  const T* c = s;
+  if constexpr (sizeof(T) == 4) c = c_tab<T, N, QC, QV>;
   Tab<T> t;
   t.eSc = c + L.eo[EO_SC]; t.eScT = c + L.eo[EO_SCT]; t.eDc = c + L.eo[EO_DC]; t.eDcT = c + L.eo[EO_DCT];
   t.eSv = c + L.eo[EO_SV]; t.eSvT = c + L.eo[EO_SVT]; t.eDv = c + L.eo[EO_DV]; t.eDvT = c + L.eo[EO_DVT];

@@ -25,8 +25,7 @@ static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -24042679
 static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                                1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                                2277821191437.0 / 14882151754819.0};
-static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
-                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+// (The stage times C_i are not needed: the operator is autonomous, the body force constant.)
 
 // ---------------------------------------------------------------------------
 // 1D polynomial tables (FP64)
@@ -971,34 +970,49 @@ int dg_cns_inverse_mass(dgcns_ctx* c, const void* in, void* out) {
   return run_op(c, OP_MASS, kp, nullptr, in, out, nullptr, nullptr);
 }
 
-int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* U_in, void* dU, double* U_out) {
-  if (!c) return DGCNS_ERR_INVALID_ARG;
-  DeviceScope ds(c);
-  (void)t;  // the operator is autonomous (constant body force)
-  if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
+// One 2N stage with coefficients (A, B): argument checks, then dU <- A dU + dt L(U_in), U_out <- U_in + B dU.
+static int stage_2n(dgcns_ctx* c, double A, double B, double dt, const double* U_in, void* dU, double* U_out) {
   if (!U_in || !dU || !U_out) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (overlap(dU, res_bytes(c), U_in, state_bytes(c)) || overlap(dU, res_bytes(c), U_out, state_bytes(c)))
     return fail(c, DGCNS_ERR_INVALID_ARG, "dU must not overlap U_in or U_out");
   if (U_in != U_out && overlap(U_in, state_bytes(c), U_out, state_bytes(c)))
     return fail(c, DGCNS_ERR_INVALID_ARG, "U_out must be U_in itself or not overlap it");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (!std::isfinite(A) || !std::isfinite(B)) return fail(c, DGCNS_ERR_INVALID_ARG, "A and B must be finite");
   if (c->prm.kernel == DGCNS_KERNEL_FUSED && U_in == U_out)
     return fail(c, DGCNS_ERR_INVALID_ARG, "fused kernel needs U_out != U_in");
   KParams kp = c->kp;
   kp.out_mode = 2;
-  kp.A = RK_A[stage];
-  kp.B = RK_B[stage];
+  kp.A = A;
+  kp.B = B;
   kp.dt = dt;
   return eval_L(c, kp, U_in, nullptr, dU, U_out);
 }
 
-int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU) {
+int dg_cns_rk_stage(dgcns_ctx* c, int stage, double dt, double t, const double* U_in, void* dU, double* U_out) {
   if (!c) return DGCNS_ERR_INVALID_ARG;
   DeviceScope ds(c);
+  (void)t;  // the operator is autonomous (constant body force)
+  if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
+  return stage_2n(c, RK_A[stage], RK_B[stage], dt, U_in, dU, U_out);
+}
+
+int dg_cns_lsrk_stage(dgcns_ctx* c, double A, double B, double dt, const double* U_in, void* dU, double* U_out) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
+  return stage_2n(c, A, B, dt, U_in, dU, U_out);
+}
+
+// nsteps steps of the 2N scheme (A, B) with `stages` stages; U holds the result.
+static int steps_2n(dgcns_ctx* c, int stages, const double* A, const double* B, int nsteps, double dt, double* U,
+                    double* U_tmp, void* dU) {
   if (nsteps < 0) return fail(c, DGCNS_ERR_INVALID_ARG, "nsteps < 0");
   if (!U || !U_tmp || !dU || overlap(U, state_bytes(c), U_tmp, state_bytes(c)) ||
       overlap(dU, res_bytes(c), U, state_bytes(c)) || overlap(dU, res_bytes(c), U_tmp, state_bytes(c)))
     return fail(c, DGCNS_ERR_INVALID_ARG, "U, U_tmp and dU must be non-NULL arrays that do not overlap");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+  for (int s = 0; s < stages; ++s)
+    if (!std::isfinite(A[s]) || !std::isfinite(B[s])) return fail(c, DGCNS_ERR_INVALID_ARG, "A and B must be finite");
   double* a = U;
   double* b = U_tmp;
   // Mixed form (fused or face-centric kernels): the stage kernel also writes float(U_out - U_ref)
@@ -1012,21 +1026,20 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
     if (rd) return rd;
   }
   for (int n = 0; n < nsteps; ++n)
-    for (int s = 0; s < 5; ++s) {
+    for (int s = 0; s < stages; ++s) {
       int r;
       if (chain) {
-        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
         KParams kp = c->kp;
         kp.out_mode = 2;
-        kp.A = RK_A[s];
-        kp.B = RK_B[s];
+        kp.A = A[s];
+        kp.B = B[s];
         kp.dt = dt;
         kp.Udev = dcur;
         kp.devOut = dnxt;
         r = eval_L(c, kp, a, nullptr, dU, b);
         std::swap(dcur, dnxt);
       } else {
-        r = dg_cns_rk_stage(c, s, dt, t0 + (n + RK_C[s]) * dt, a, dU, b);
+        r = stage_2n(c, A[s], B[s], dt, a, dU, b);
       }
       if (r) return r;
       std::swap(a, b);
@@ -1036,6 +1049,22 @@ int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, d
       return cuda_fail(c, "state copy");
   }
   return DGCNS_OK;
+}
+
+int dg_cns_rk_steps(dgcns_ctx* c, int nsteps, double dt, double t0, double* U, double* U_tmp, void* dU) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
+  (void)t0;  // the operator is autonomous (constant body force)
+  return steps_2n(c, 5, RK_A, RK_B, nsteps, dt, U, U_tmp, dU);
+}
+
+int dg_cns_lsrk_steps(dgcns_ctx* c, int stages, const double* A, const double* B, int nsteps, double dt, double* U,
+                      double* U_tmp, void* dU) {
+  if (!c) return DGCNS_ERR_INVALID_ARG;
+  DeviceScope ds(c);
+  if (stages < 1 || stages > DGCNS_MAX_STAGES || !A || !B)
+    return fail(c, DGCNS_ERR_INVALID_ARG, "stages must be 1..DGCNS_MAX_STAGES with host arrays A and B");
+  return steps_2n(c, stages, A, B, nsteps, dt, U, U_tmp, dU);
 }
 
 // Adjoint VJP kernel(s) for Y in d_R: the face-centric organisation first writes the face shares.

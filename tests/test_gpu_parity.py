@@ -505,3 +505,29 @@ def test_overlapping_arrays_are_rejected_before_any_launch():
     assert lib.dg_cns_apply(g.ctx, p(0), p(n), api.OP_L) == 0
     torch.cuda.synchronize()
     assert torch.equal(buf[n:2 * n].reshape(U.shape), g.apply(U))
+
+
+def test_lsrk_stage_and_steps_general_2n_schemes():
+    """dg_cns_lsrk_stage with a stage's RK(5,4) coefficients is dg_cns_rk_stage, dg_cns_lsrk_steps with the
+    RK(5,4) table is dg_cns_rk_steps (bit for bit), and Williamson's 3-stage scheme matches the oracle's 2N
+    step at 1e-12 (face-centric and fused kernels)."""
+    from oracle import rk as ork
+    from paper_1806_03095_gb300 import schemes
+    for kernel in (1, 2):
+        g, op = pair((3, 2, 4), 3, kernel=kernel)
+        U0 = on_gpu(inputs.tgv_state(op.xyz) + 1e-3 * inputs.uniform((op.mesh.Nc, 5, op.mesh.n ** 3), 19))
+        dU0 = on_gpu(inputs.uniform(U0.shape, 20))
+        dt = 2e-3
+        Ua, dUa, Ub, dUb = g.empty_state(), dU0.clone(), g.empty_state(), dU0.clone()
+        g.rk_stage(2, dt, 0.0, U0, dUa, Ua)
+        g.lsrk_stage(schemes.LSRK54[0][2], schemes.LSRK54[1][2], dt, U0, dUb, Ub)
+        assert torch.equal(Ua, Ub) and torch.equal(dUa, dUb)
+        assert torch.equal(g.rk_steps(2, dt, 0.0, U0.clone()), g.lsrk_steps(schemes.LSRK54, 2, dt, U0.clone()))
+        got = g.lsrk_steps(schemes.LSRK33, 3, dt, U0.clone())
+        U = U0.cpu()
+        for n in range(3):
+            U = ork.lsrk_step(lambda V, t: op.L(V), U, dt, n * dt, ork.LSRK33_A, ork.LSRK33_B, ork.LSRK33_C)
+        l2, mx = rel_err(got, U)
+        assert l2 < TOL64 and mx < TOL64, (kernel, l2, mx)
+        with pytest.raises(Exception):
+            g.lsrk_steps(((0.0, float("nan")), (0.5, 0.5)), 1, dt, U0.clone())

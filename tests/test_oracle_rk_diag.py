@@ -51,6 +51,61 @@ def test_lsrk54_negative_control_typo_breaks_order():
     assert abs(float(sum(b) - 1)) > 1e-13
 
 
+def _conditions(a, b, c):
+    s = len(b)
+    return {
+        "sum b": (sum(b), Fraction(1)),
+        "b c": (sum(b[i] * c[i] for i in range(s)), Fraction(1, 2)),
+        "b c^2": (sum(b[i] * c[i] ** 2 for i in range(s)), Fraction(1, 3)),
+        "b a c": (sum(b[i] * a[i][j] * c[j] for i in range(s) for j in range(s)), Fraction(1, 6)),
+        "b c^3": (sum(b[i] * c[i] ** 3 for i in range(s)), Fraction(1, 4)),
+        "b a a c": (sum(b[i] * a[i][j] * a[j][l] * c[l] for i in range(s) for j in range(s) for l in range(s)),
+                    Fraction(1, 24)),
+    }
+
+
+def test_lsrk33_third_order_exactly_and_not_fourth():
+    """Williamson's 2N scheme: the Butcher tableau from (A, B) meets the four conditions of order <= 3
+    exactly (rational arithmetic), reproduces the stage times C, and misses order 4."""
+    a, b = rk.butcher_from_2n(rk.LSRK33_A, rk.LSRK33_B)
+    c = [sum(row) for row in a]
+    assert c == list(rk.LSRK33_C)
+    conds = _conditions(a, b, c)
+    for name in ("sum b", "b c", "b c^2", "b a c"):
+        assert conds[name][0] == conds[name][1], name
+    assert any(conds[n][0] != conds[n][1] for n in ("b c^3", "b a a c"))
+
+
+def test_lsrk33_negative_control_typo():
+    a, b = rk.butcher_from_2n((Fraction(0), Fraction(-5, 9), Fraction(-153, 127)), rk.LSRK33_B)
+    c = [sum(row) for row in a]
+    conds = _conditions(a, b, c)
+    assert any(conds[n][0] != conds[n][1] for n in ("sum b", "b c", "b c^2", "b a c"))
+
+
+def test_lsrk33_scalar_ode_order_3():
+    lam = -1.3
+    errs = []
+    for nst in (10, 20, 40):
+        dt = 1.0 / nst
+        y = torch.tensor(1.0, dtype=torch.float64)
+        for i in range(nst):
+            y = rk.lsrk_step(lambda v, t: lam * v, y, dt, i * dt, rk.LSRK33_A, rk.LSRK33_B, rk.LSRK33_C)
+        errs.append(abs(float(y) - math.exp(lam)))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert abs(math.log2(e0 / e1) - 3.0) < 0.15
+
+
+def test_lsrk_step_with_rk54_coefficients_is_step():
+    op = DGOperator(BoxMesh((2, 2, 2), [-math.pi] * 3, [math.pi] * 3, (1, 1, 1), 2), ph.Physics.from_numbers(1600.0, 0.71, 0.1),
+                    4, 3)
+    U = inputs.tgv_state(op.xyz)
+    Lf = lambda V, t: op.L(V)  # noqa: E731
+    a = rk.step(Lf, U, 1e-3, 0.0)
+    b = rk.lsrk_step(Lf, U, 1e-3, 0.0, rk.LSRK54_A, rk.LSRK54_B, rk.LSRK54_C)
+    assert torch.equal(a, b)
+
+
 def test_lsrk54_scalar_ode_order_4():
     lam = -1.3
     errs = []
