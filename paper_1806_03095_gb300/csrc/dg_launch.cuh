@@ -6,6 +6,7 @@
 #include "dg_adjoint.cuh"
 #include "dg_adjoint_faces.cuh"
 #include "dg_faces.cuh"
+#include "dg_faces_fp32.cuh"
 #include "dg_kernels.cuh"
 #include "dg_mass.cuh"
 #include "dg_launchers.h"
@@ -23,6 +24,11 @@ namespace dgcns {
 #endif
 #ifndef DGCNS_FP64_FACE_THREADS
 #define DGCNS_FP64_FACE_THREADS 256
+#endif
+// FP32 affine face terms at k = 3 by the register-resident task kernel (dg_faces_fp32.cuh); 0 keeps the
+// warp-per-face kernel (for comparison)
+#ifndef DGCNS_FP32_TASK_FACES
+#define DGCNS_FP32_TASK_FACES 1
 #endif
 
 // Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
@@ -1202,6 +1208,9 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     if (kp.periodic[d]) continue;
     const int plane = kp.nc[d == 0 ? 1 : 0] * kp.nc[d == 2 ? 1 : 2];
     if (plane > extra_items) extra_items = plane;
+  }
+  if constexpr (sizeof(T) == 4 && GEO == GEO_AFFINE && DGCNS_FP32_TASK_FACES && task_faces_ok<N, QC, QV>()) {
+    if (kp.Udev != nullptr) return launch_task_faces<N, QC, QV>(kp, FB, st);
   }
   if constexpr (sizeof(T) == 4) {
     constexpr int WPC = 8;

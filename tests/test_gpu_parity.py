@@ -531,3 +531,22 @@ def test_lsrk_stage_and_steps_general_2n_schemes():
         assert l2 < TOL64 and mx < TOL64, (kernel, l2, mx)
         with pytest.raises(Exception):
             g.lsrk_steps(((0.0, float("nan")), (0.5, 0.5)), 1, dt, U0.clone())
+
+
+@pytest.mark.parametrize("what", ["F", "FC", "FV"])
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
+@pytest.mark.parametrize("k", [3, 4])
+def test_mixed_face_centric_random_states(k, periodic, what):
+    """The mixed form's face-centric kernels (FP32 arithmetic) on random states: independent nodal draws give
+    jumps on every face and no cancellation between the weak-form terms, so F, F_c and F_v agree with the
+    FP64 oracle to FP32 accuracy (2-norm 1e-5, max 1e-4 relative).  A ragged 3x4x5 box, periodic or with
+    walls on all six sides (lower and upper wall faces of every direction)."""
+    lo, hi = (-1.0, -1.5, -2.0), (2.0, 1.5, 2.5)
+    g, op = pair((3, 4, 5), k, precision=1, kernel=2, periodic=periodic, lo=lo, hi=hi)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 23)
+    op_code = {"F": api.OP_F, "FC": api.OP_FC, "FV": api.OP_FV}[what]
+    which = {"F": WHAT_ALL, "FC": WHAT_CONV, "FV": WHAT_VISC}[what]
+    out = g.apply(on_gpu(U), op=op_code)
+    ref = op.residual(U, which)
+    l2, mx = rel_err(out, ref)
+    assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
