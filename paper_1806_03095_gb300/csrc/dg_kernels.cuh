@@ -1087,4 +1087,32 @@ __device__ void inverse_mass(const T* su, T* sr, T* ma, const Tab<T>& tb, const 
   }
 }
 
+// 2N update of a batch: dU <- A dU + dt L (residual type), U_out <- U + B dU (FP64); the loads of U and
+// dU of a thread are issued together before the stores.  With kp.devOut (mixed form inside a
+// multi-step call) also float(U_out - U_ref), the deviation state the next stage reads.
+template <int PER, int N3, typename T>
+__device__ __forceinline__ void stage_update(const KParams& kp, const double* U, T* dU, double* Uout, const T* sr,
+                                             size_t base, int nvals, int rank, int stride) {
+  struct UD {
+    double u;
+    T d;
+  };
+  const T A = T(kp.A), dt = T(kp.dt);
+  const double B = kp.B;
+  const bool readD = kp.A != 0.0;
+  T* dev = static_cast<T*>(kp.devOut);
+  batched_pass<PER>(rank, stride, nvals,
+                    [&](int i) { return UD{U[base + i], readD ? dU[base + i] : T(0)}; },
+                    [&](int i, UD v) {
+                      const T du = A * v.d + dt * sr[i];
+                      dU[base + i] = du;
+                      const double uo = v.u + B * double(du);
+                      Uout[base + i] = uo;
+                      if (dev) {
+                        const int c = (i / N3) % 5;
+                        dev[base + i] = T(uo - (c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0)));
+                      }
+                    });
+}
+
 }  // namespace dgcns

@@ -6,6 +6,7 @@
 #include "dg_adjoint.cuh"
 #include "dg_adjoint_faces.cuh"
 #include "dg_faces.cuh"
+#include "dg_cell_fp32.cuh"
 #include "dg_faces_fp32.cuh"
 #include "dg_kernels.cuh"
 #include "dg_mass.cuh"
@@ -29,6 +30,11 @@ namespace dgcns {
 // warp-per-face kernel (for comparison)
 #ifndef DGCNS_FP32_TASK_FACES
 #define DGCNS_FP32_TASK_FACES 1
+#endif
+// FP32 affine face-centric cell + mass stage at k = 3 by the register-resident task kernel
+// (dg_cell_fp32.cuh); 0 keeps the warp-per-cell kernel (for comparison)
+#ifndef DGCNS_FP32_TASK_CELL
+#define DGCNS_FP32_TASK_CELL 1
 #endif
 
 // Cells per CTA: the largest batch (<= 4 for FP32, <= DGCNS_FP64_CELL_CAP for FP64) whose shared
@@ -88,34 +94,6 @@ constexpr size_t op_smem_bytes() {
                        op_arena_elems<N, QC, QV, CB, CELL, FACE, MASS, GEO>() +
                        op_geo_elems<N, QC, QV, CB, FACE, GEO>() + 2 * CB;
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
-}
-
-// 2N update of a batch: dU <- A dU + dt L (residual type), U_out <- U + B dU (FP64); the loads of U and
-// dU of a thread are issued together before the stores.  With kp.devOut (mixed form inside a
-// multi-step call) also float(U_out - U_ref), the deviation state the next stage reads.
-template <int PER, int N3, typename T>
-__device__ __forceinline__ void stage_update(const KParams& kp, const double* U, T* dU, double* Uout, const T* sr,
-                                             size_t base, int nvals, int rank, int stride) {
-  struct UD {
-    double u;
-    T d;
-  };
-  const T A = T(kp.A), dt = T(kp.dt);
-  const double B = kp.B;
-  const bool readD = kp.A != 0.0;
-  T* dev = static_cast<T*>(kp.devOut);
-  batched_pass<PER>(rank, stride, nvals,
-                    [&](int i) { return UD{U[base + i], readD ? dU[base + i] : T(0)}; },
-                    [&](int i, UD v) {
-                      const T du = A * v.d + dt * sr[i];
-                      dU[base + i] = du;
-                      const double uo = v.u + B * double(du);
-                      Uout[base + i] = uo;
-                      if (dev) {
-                        const int c = (i / N3) % 5;
-                        dev[base + i] = T(uo - (c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0)));
-                      }
-                    });
 }
 
 // component c of the reference state U_ref = (rho_r, 0, 0, 0, rho_r c_v T_0)
@@ -914,6 +892,10 @@ int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Ri
     case OP_CELL | OP_FACE:
       return launch_op_any<T, N, QC, QV, GEO, WARP, true, true, false>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_CELL | OP_MASS:
+      if constexpr (sizeof(T) == 4 && GEO == GEO_AFFINE && DGCNS_FP32_TASK_CELL && task_cell_ok<N, QC, QV>()) {
+        if (kp.fbuf != nullptr && kp.Udev != nullptr && !kp.has_bf && (kp.out_mode == 1 || kp.out_mode == 2))
+          return launch_task_cell<N, QC, QV>(kp, U, Rout, dU, Uout, st);
+      }
       if constexpr (Feat<N, QC, QV>::faces)
         return launch_op_any<T, N, QC, QV, GEO, WARP, true, false, true>(kp, U, Rin, Rout, dU, Uout, st);
       return -2;

@@ -550,3 +550,30 @@ def test_mixed_face_centric_random_states(k, periodic, what):
     ref = op.residual(U, which)
     l2, mx = rel_err(out, ref)
     assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
+@pytest.mark.parametrize("k", [3, 4])
+def test_mixed_face_centric_L_and_stage_random_states(k, periodic):
+    """The mixed form's face-centric cell + inverse-mass + stage kernel on random states against the FP64
+    oracle: L(U) to FP32 accuracy (2-norm 1e-5, max 1e-4 relative), and one RK stage (stage 3: dU is read):
+    dU to the same bound, and U_out - U = B dU with the FP32 dU accumulated in FP64 (1e-10).  Ragged 3x4x5
+    box, periodic or with walls on all six sides."""
+    lo, hi = (-1.0, -1.5, -2.0), (2.0, 1.5, 2.5)
+    g, op = pair((3, 4, 5), k, precision=1, kernel=2, periodic=periodic, lo=lo, hi=hi)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 24)
+    Lref = op.L(U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), Lref)
+    assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
+    dU0 = inputs.uniform(U.shape, 25)
+    dt = 1e-3
+    dUg, Uo = on_gpu(dU0).float().contiguous(), g.empty_state()
+    g.rk_stage(3, dt, 0.0, on_gpu(U), dUg, Uo)
+    dU_ref = ork.A[3] * dU0.float().double() + dt * Lref
+    l2, mx = rel_err(dUg, dU_ref)
+    assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
+    # the state is accumulated in FP64: U_out - U is B times the FP32 dU, rounded at the ulp of U (~3e-14
+    # of 178) against an increment of order B; an FP32 accumulation would miss this by 1e-6
+    inc = (Uo.cpu() - U)
+    l2, mx = rel_err(inc, ork.B[3] * dUg.double().cpu())
+    assert l2 < 1e-10 and mx < 1e-10, (l2, mx)
