@@ -569,33 +569,38 @@ def inverse_mass_only(args):
 
 
 def k_sweep(steps=2):
-    """Throughput against the polynomial degree (the paper's throughput-versus-k study, Sec. 3): TGV meshes of
-    about 84M DoFs for k = 2..6 (FP64) and k = 3..5 (mixed), fused and face-centric kernels, and (k = 2..5, FP64,
-    face-centric) with the paper's own quadrature, the 3/2 rule on both terms."""
+    """Throughput against the polynomial degree (the paper's throughput-versus-k study, Sec. 4.1.2): TGV meshes
+    of about 84M DoFs for k = 2..7 (FP64; k = 3..5 also mixed), fused and face-centric kernels (k = 7:
+    face-centric only), and FP64 face-centric with the paper's 3/2 rule on both terms (k = 2..5) and the
+    2k+1 rule on both terms (k = 2..4)."""
     from paper_1806_03095_gb300 import configs
     device = torch.cuda.current_device()
     out = {}
-    for k in (2, 3, 4, 5, 6):
+
+    def run(key, cfg):
+        ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+        nodes = bufs[0].numel() // 5
+        n = cfg["ncells"][0]
+        out[key] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps), "unit": UNIT,
+                    "nq": [cfg["nq_conv"], cfg["nq_visc"]]}
+        del ctx, bufs
+        torch.cuda.empty_cache()
+
+    for k in (2, 3, 4, 5, 6, 7):
         n = max(2, int(round((16.78e6 / (k + 1) ** 3) ** (1.0 / 3.0))))
         for prec in ((0, 1) if k in (3, 4, 5) else (0,)):
-            for kern in (1, 2):
-                cfg = configs.tgv(n, k, precision=prec, kernel=kern)
-                ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
-                nodes = bufs[0].numel() // 5
+            for kern in ((1, 2) if k <= 6 else (2,)):
                 key = "k%d_%s_%s" % (k, "fp64" if prec == 0 else "mixed", "fused" if kern == 1 else "faces")
-                out[key] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps), "unit": UNIT}
-                del ctx, bufs
-                torch.cuda.empty_cache()
+                run(key, configs.tgv(n, k, precision=prec, kernel=kern))
         if k <= 5:
             # the paper's own quadrature: the 3/2 rule on the viscous term too
             cfg = dict(configs.tgv(n, k, precision=0, kernel=2))
             cfg["nq_visc"] = cfg["nq_conv"]
-            ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
-            nodes = bufs[0].numel() // 5
-            out["k%d_fp64_faces_3/2_rule_both_terms" % k] = {"cells": "%d^3" % n, "value": _rate(ms, nodes, steps),
-                                                              "unit": UNIT, "nq": [cfg["nq_conv"], cfg["nq_visc"]]}
-            del ctx, bufs
-            torch.cuda.empty_cache()
+            run("k%d_fp64_faces_3/2_rule_both_terms" % k, cfg)
+        if k <= 4:
+            cfg = dict(configs.tgv(n, k, precision=0, kernel=2))
+            cfg["nq_conv"] = cfg["nq_visc"] = 2 * k + 1
+            run("k%d_fp64_faces_2k+1_rule_both_terms" % k, cfg)
     return out
 
 

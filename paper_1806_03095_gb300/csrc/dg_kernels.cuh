@@ -534,7 +534,11 @@ struct Sizes {
   static constexpr int N2 = N * N;
   static constexpr int N3 = N * N * N;
   static constexpr int QC3 = QC * QC * QC, QV3 = QV * QV * QV;
-  static constexpr int CELL_ARENA = 20 * (QC3 > QV3 ? QC3 : QV3);  // per cell
+  // LEAN: the convective cell term forms one flux direction at a time (15 QC^3 values per cell instead of
+  // 20 QC^3), used where the full arena would not fit (QC >= 11: 213 KB per cell in FP64)
+  static constexpr bool LEAN = 20 * QC3 * 8 > 160 * 1024;
+  static constexpr int CELL_ARENA = LEAN ? (15 * QC3 > 20 * QV3 ? 15 * QC3 : 20 * QV3)
+                                         : 20 * (QC3 > QV3 ? QC3 : QV3);  // per cell
   // face arena per cell: conv: 2 layers, tmp, 2 point arrays; visc: 4 layers, tmp, 8 point arrays
   static constexpr int FACE_CONV = 2 * 5 * N2 + 5 * QC * N + 2 * 5 * QC * QC;
   static constexpr int FACE_VISC = 4 * 5 * N2 + 5 * QV * N + 8 * 5 * QV * QV;
@@ -566,7 +570,67 @@ __device__ void cell_terms(const T* su, T* sr, T* ar, const Tab<T>& tb, const KP
   const T detJ = kc.detJ;
   const T hinv[3] = {kc.hinv[0], kc.hinv[1], kc.hinv[2]};
   const int nbl = nb * 5;
-  if (kp.conv) {
+  if constexpr (Sizes<N, QC, QV>::LEAN) {
+    if (kp.conv) {
+      static_assert(GEO != GEO_FLY, "the lean convective term has no geometry-on-the-fly variant");
+      constexpr int P = QC * QC * QC;
+      const T* gcell = static_cast<const T*>(kp.gcc) + (size_t)e0 * 10 * P;
+      T* Uq = ar;
+      T* Fj = ar + CB * 5 * P;
+      T* Gt = ar + 2 * CB * 5 * P;
+      // interpolate to the convective Gauss grid (temporaries in Fj and Gt)
+      sweep<T, 0, N, N, N, QC, 1, false>(su, Fj, tb.eSc, nbl, grp);
+      grp.sync();
+      sweep<T, 1, QC, N, N, QC, 1, false>(Fj, Gt, tb.eSc, nbl, grp);
+      grp.sync();
+      sweep<T, 2, QC, QC, N, QC, 1, false>(Gt, Uq, tb.eSc, nbl, grp);
+      grp.sync();
+      // one direction b at a time: the contravariant flux -F_c J^{-T} |J| w along b, then Gt += D_b^T of it
+#pragma unroll 1
+      for (int b = 0; b < 3; ++b) {
+        for (int idx = grp.rank(); idx < nb * P; idx += grp.size()) {
+          const int e = idx / P, p = idx - e * P;
+          const int q0 = p % QC, q1 = (p / QC) % QC, q2 = p / (QC * QC);
+          T u[5];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) u[c] = Uq[(e * 5 + c) * P + p];
+          const T rinv = T(1) / (ph.rho_r + u[0]);
+          const T dp = pressure_dev(u, rinv, ph.gm1);
+          if (GEO == GEO_AFFINE) {
+            T f[5];
+            conv_flux_dir(u, rinv, dp, ph.H_r, b, f);
+            const T sc = -tb.wc[q0] * tb.wc[q1] * tb.wc[q2] * detJ * hinv[b];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) Fj[(e * 5 + c) * P + p] = sc * f[c];
+          } else {
+            const T* g = gcell + (size_t)e * 10 * P + p;
+            const T j0 = g[(3 * b) * P], j1 = g[(3 * b + 1) * P], j2 = g[(3 * b + 2) * P];
+            const T jw = -g[9 * P] * tb.wc[q0] * tb.wc[q1] * tb.wc[q2];
+            T F[3][5];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) conv_flux_dir(u, rinv, dp, ph.H_r, a, F[a]);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) Fj[(e * 5 + c) * P + p] = jw * (j0 * F[0][c] + j1 * F[1][c] + j2 * F[2][c]);
+          }
+        }
+        grp.sync();
+        if (b == 0)
+          sweep<T, 0, QC, QC, QC, QC, -1, false>(Fj, Gt, tb.eDcT, nbl, grp);
+        else if (b == 1)
+          sweep<T, 1, QC, QC, QC, QC, -1, true>(Fj, Gt, tb.eDcT, nbl, grp);
+        else
+          sweep<T, 2, QC, QC, QC, QC, -1, true>(Fj, Gt, tb.eDcT, nbl, grp);
+        grp.sync();
+      }
+      // back to the nodes: S^T along z, y, x
+      sweep<T, 2, QC, QC, QC, N, 1, false>(Gt, Fj, tb.eScT, nbl, grp);
+      grp.sync();
+      sweep<T, 1, QC, QC, N, N, 1, false>(Fj, Uq, tb.eScT, nbl, grp);
+      grp.sync();
+      sweep<T, 0, QC, N, N, N, 1, true>(Uq, sr, tb.eScT, nbl, grp);
+      grp.sync();
+    }
+  } else if (kp.conv) {
     constexpr int P = QC * QC * QC;
     // stored geometry of the CTA's cells: global arrays, or recomputed now into `go` (GEO_FLY)
     const T* gcell = GEO == GEO_FLY ? go : static_cast<const T*>(kp.gcc) + (size_t)e0 * 10 * P;

@@ -62,9 +62,10 @@ struct Launchers {
 };
 
 // (N = k+1, QC, QV) triples compiled into the library.  Default rules:
-// QC = floor(3k/2)+1 (3/2-rule, Sec. 2.2.3) and QV = k+1; plus the standard
-// rule QC = QV = k+1 at k = 3, 5 and the paper's own setting with the 3/2 rule on
-// both terms (QV = QC) at k = 2..5.
+// QC = floor(3k/2)+1 (3/2-rule, Sec. 2.2.3) and QV = k+1 (k = 1..7); plus the
+// standard rule QC = QV = k+1 at k = 3, 5, the paper's own setting with the 3/2
+// rule on both terms (QV = QC) at k = 2..5, and the 2k+1 rule on both terms
+// (QC = QV = 2k+1) at k = 2..4 (Sec. 4.1.2, over-integration).
 #define DGCNS_CONFIGS(X) \
   X(2, 2, 2)             \
   X(3, 4, 3)             \
@@ -72,12 +73,16 @@ struct Launchers {
   X(5, 7, 5)             \
   X(6, 8, 6)             \
   X(7, 10, 7)            \
+  X(8, 11, 8)            \
   X(4, 4, 4)             \
   X(6, 6, 6)             \
   X(3, 4, 4)             \
   X(4, 5, 5)             \
   X(5, 7, 7)             \
-  X(6, 8, 8)
+  X(6, 8, 8)             \
+  X(3, 5, 5)             \
+  X(4, 7, 7)             \
+  X(5, 9, 9)
 
 // Parts of each instantiation (separate translation units): FP64 operator, FP32 operator,
 // diagnostics + geometry, adjoint, FP64 face kernel, FP32 face kernel, adjoint face kernels.

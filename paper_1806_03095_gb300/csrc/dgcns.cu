@@ -1175,7 +1175,9 @@ int dg_cns_diagnostics(dgcns_ctx* c, const double* U, const void* LU, double* ou
   const DiagFn f = c->prm.precision == DGCNS_MIXED ? c->L.diag_fp32 : c->L.diag_fp64;
   {
     TimedScope ts(c, DGCNS_KT_OTHER);
-    if (f(kp, U, LU, c->d_partial, &nblk, c->stream) != 0) return cuda_fail(c, "diagnostics kernel launch");
+    const int r = f(kp, U, LU, c->d_partial, &nblk, c->stream);
+    if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "diagnostics kernel does not fit shared memory for this (k, nq)");
+    if (r != 0) return cuda_fail(c, "diagnostics kernel launch");
   }
   c->launches += 1;
   std::vector<double> part((size_t)nblk * 10);

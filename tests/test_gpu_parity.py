@@ -125,6 +125,19 @@ def test_other_quadrature_rules(k, qc, qv, kernel):
     assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
+@pytest.mark.parametrize("k,qc,qv", [(2, 5, 5), (3, 7, 7), (4, 9, 9), (7, 11, 8)])
+def test_over_integration_and_degree_seven(k, qc, qv):
+    """The 2k+1 rule on both terms at k = 2, 3, 4 (Sec. 4.1.2, over-integration) and k = 7 with the 3/2 rule
+    (the convective cell term formed one direction at a time, 15 n_q^3 values per cell), face-centric
+    kernels, FP64: F and L against the oracle at 1e-12 on a ragged box of 2x3x2 cells."""
+    g, op = pair((2, 3, 2), k, qc, qv, kernel=2)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 26 + k)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_single_cell_periodic_box(kernel):
     """Degenerate mesh: one cell per direction, the cell is its own neighbour on every face."""
