@@ -259,7 +259,7 @@ def main():
         out["clocks"] = clk
 
     if rank == 0 and ws == 1:
-        out["e2e"] = e2e_native(ctx, bufs, dt, min(args.steps, 3))
+        out["e2e"] = e2e_native(ctx, bufs, dt, min(args.steps, 10))
         if not args.no_extras:
             out["cpu_baseline"] = cpu_baseline(cfg)
             out["extras"] = extras(args, cfg)
