@@ -880,6 +880,14 @@ int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Ri
     case OP_CELL: return launch_op_any<T, N, QC, QV, GEO, WARP, true, false, false>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_FACE: return launch_op_any<T, N, QC, QV, GEO, WARP, false, true, false>(kp, U, Rin, Rout, dU, Uout, st);
     case OP_MASS:
+      if constexpr (sizeof(T) == 4 && GEO == GEO_AFFINE && mass_reg_ok<N, QC, QV>()) {
+        // FP32 at k = 3: every block in registers (16-byte aligned arrays, no body force)
+        const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+        if (!kp.has_bf && al(Rin) && al(Rout) && al(dU) && al(U) && al(Uout)) {
+          if (kp.out_mode == 2) return launch_mass_reg<N, QC, QV, true>(kp, Rin, Rout, dU, U, Uout, st);
+          return launch_mass_reg<N, QC, QV, false>(kp, Rin, Rout, dU, U, Uout, st);
+        }
+      }
       if constexpr (mass_tma_ok<T, N>() && GEO != GEO_FLY) {
         // the TMA-pipelined kernel needs 16-byte aligned arrays and no body force (no state read)
         const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };

@@ -8,6 +8,7 @@
 #pragma once
 #include <cstdint>
 
+#include "dg_faces_fp32.cuh"
 #include "dg_kernels.cuh"
 
 namespace dgcns {
@@ -273,4 +274,175 @@ int launch_mass_tma(const KParams& kp, const void* Rin, void* Rout, void* dU, co
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+
+// ---------------------------------------------------------------------------
+// M^{-1} of FP32 data at k = 3 (affine): one (cell, component) block of N^3 = 64 values per thread, the six
+// 1D sweeps and the scaling in registers (S^-T along x, y, z; 1 / (|J| w); S^-1 along x, y, z).  A CTA
+// takes 128 consecutive blocks (one contiguous range): coalesced 16-byte loads into shared memory rows
+// padded to N^3 + 4 floats (so the 16-byte row reads of 8 neighbouring threads meet distinct banks),
+// the per-thread sweeps, and coalesced 16-byte stores; with STAGE the 2N update (and the next deviation
+// state when kp.devOut is set) runs in that store pass.  No shared-memory traffic inside the sweeps, so
+// the kernel is bound by HBM.  out_mode 0: Rout = M^-1 Rin; 1: Rout = -M^-1 Rin; STAGE: L = -M^-1 Rin.
+// Rin may alias Rout and U may alias Uout (a CTA reads its whole range before it writes).
+// ---------------------------------------------------------------------------
+constexpr int kMassRegThreads = 128;
+
+template <int N>
+__device__ __forceinline__ void mass_block_regs(float (&x)[N * N * N], const Tab<float>& tb, float sg_detJinv) {
+  constexpr int N2 = N * N;
+  // S^-T along x (index 0), y, z
+#pragma unroll
+  for (int l = 0; l < N2; ++l) {
+    float a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = x[l * N + i];
+    eo_apply<N, N, 1>(tb.eSmiT, a, b);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[l * N + i] = b[i];
+  }
+#pragma unroll
+  for (int z = 0; z < N; ++z)
+#pragma unroll
+    for (int i0 = 0; i0 < N; ++i0) {
+      float a[N], b[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = x[z * N2 + i * N + i0];
+      eo_apply<N, N, 1>(tb.eSmiT, a, b);
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[z * N2 + i * N + i0] = b[i];
+    }
+  float iw[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) iw[i] = 1.f / tb.wm[i];
+#pragma unroll
+  for (int l = 0; l < N2; ++l) {
+    float a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = x[i * N2 + l];
+    eo_apply<N, N, 1>(tb.eSmiT, a, b);
+    const float wl = iw[l % N] * iw[l / N] * sg_detJinv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[i] *= wl * iw[i];
+    eo_apply<N, N, 1>(tb.eSmi, b, a);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i * N2 + l] = a[i];
+  }
+  // S^-1 along y, x
+#pragma unroll
+  for (int z = 0; z < N; ++z)
+#pragma unroll
+    for (int i0 = 0; i0 < N; ++i0) {
+      float a[N], b[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = x[z * N2 + i * N + i0];
+      eo_apply<N, N, 1>(tb.eSmi, a, b);
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[z * N2 + i * N + i0] = b[i];
+    }
+#pragma unroll
+  for (int l = 0; l < N2; ++l) {
+    float a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = x[l * N + i];
+    eo_apply<N, N, 1>(tb.eSmi, a, b);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[l * N + i] = b[i];
+  }
+}
+
+template <int N, int QC, int QV, bool STAGE>
+__global__ void __launch_bounds__(kMassRegThreads) dg_mass_reg_kernel(const KParams kp, const double* U,
+                                                                      const float* Rin, float* Rout, float* dU,
+                                                                      double* Uout) {
+  constexpr int N3 = N * N * N, V4 = N3 / 4, RS = N3 + 4, NB = kMassRegThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* stab = reinterpret_cast<float*>(smem_raw);
+  float* sb = stab + ((table_elems<N, QC, QV>() + 3) & ~3);  // [NB][RS]
+  const long long nblocks = (long long)kp.Nc * 5;
+  const long long b0 = (long long)blockIdx.x * NB;
+  if (b0 >= nblocks) return;
+  const int nb = (int)min((long long)NB, nblocks - b0);
+  const Tab<float> tb = load_tables<float, N, QC, QV>(static_cast<const float*>(kp.tables), stab);
+  const size_t base = (size_t)b0 * N3;
+  const float4* src = reinterpret_cast<const float4*>(Rin + base);
+  batched_pass<(NB * V4 + kMassRegThreads - 1) / kMassRegThreads>(
+      threadIdx.x, kMassRegThreads, nb * V4, [&](int f) { return src[f]; },
+      [&](int f, float4 v) { reinterpret_cast<float4*>(sb + (f / V4) * RS)[f % V4] = v; });
+  __syncthreads();
+  if ((int)threadIdx.x < nb) {
+    float x[N3];
+    float* row = sb + threadIdx.x * RS;
+    vec_load<float, N3>(row, x);
+    const float sg = (STAGE || kp.out_mode != 0) ? -1.f : 1.f;
+    mass_block_regs<N>(x, tb, sg / kconst<float>(kp).detJ);
+    vec_store<float, N3>(row, x);
+  }
+  __syncthreads();
+  if (!STAGE) {
+    float4* dst = reinterpret_cast<float4*>(Rout + base);
+    for (int f = threadIdx.x; f < nb * V4; f += kMassRegThreads)
+      dst[f] = reinterpret_cast<const float4*>(sb + (f / V4) * RS)[f % V4];
+    return;
+  }
+  const float A = float(kp.A), dt = float(kp.dt);
+  const double B = kp.B;
+  const bool readD = kp.A != 0.0;
+  float* dev = static_cast<float*>(kp.devOut);
+  struct In {
+    float4 d;
+    double2 u0, u1;
+  };
+  batched_pass<(NB * V4 + kMassRegThreads - 1) / kMassRegThreads>(
+      threadIdx.x, kMassRegThreads, nb * V4,
+      [&](int f) {
+        In v;
+        v.d = readD ? reinterpret_cast<const float4*>(dU + base)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v.u0 = reinterpret_cast<const double2*>(U + base)[2 * f];
+        v.u1 = reinterpret_cast<const double2*>(U + base)[2 * f + 1];
+        return v;
+      },
+      [&](int f, In v) {
+        const float4 L = reinterpret_cast<const float4*>(sb + (f / V4) * RS)[f % V4];
+        float4 d;
+        d.x = A * v.d.x + dt * L.x;
+        d.y = A * v.d.y + dt * L.y;
+        d.z = A * v.d.z + dt * L.z;
+        d.w = A * v.d.w + dt * L.w;
+        reinterpret_cast<float4*>(dU + base)[f] = d;
+        double2 o0, o1;
+        o0.x = v.u0.x + B * double(d.x);
+        o0.y = v.u0.y + B * double(d.y);
+        o1.x = v.u1.x + B * double(d.z);
+        o1.y = v.u1.y + B * double(d.w);
+        reinterpret_cast<double2*>(Uout + base)[2 * f] = o0;
+        reinterpret_cast<double2*>(Uout + base)[2 * f + 1] = o1;
+        if (dev != nullptr) {
+          const int c = (int)(((b0 + f / V4)) % 5);
+          const double ref = c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0);
+          reinterpret_cast<float4*>(dev + base)[f] =
+              make_float4(float(o0.x - ref), float(o0.y - ref), float(o1.x - ref), float(o1.y - ref));
+        }
+      });
+}
+
+template <int N, int QC, int QV>
+constexpr bool mass_reg_ok() {
+  return N == 4;
+}
+
+template <int N, int QC, int QV, bool STAGE>
+int launch_mass_reg(const KParams& kp, const void* Rin, void* Rout, void* dU, const double* U, double* Uout,
+                    cudaStream_t st) {
+  constexpr size_t smem =
+      ((size_t)((table_elems<N, QC, QV>() + 3) & ~3) + (size_t)kMassRegThreads * (N * N * N + 4)) * sizeof(float) + 64;
+  static_assert(smem <= 227 * 1024, "register mass kernel shared memory");
+  auto k = dg_mass_reg_kernel<N, QC, QV, STAGE>;
+  static bool attr[kMaxDevices] = {};
+  if (smem_attr_once(k, smem, attr)) return -1;
+  const long long nblocks = (long long)kp.Nc * 5;
+  const int grid = (int)((nblocks + kMassRegThreads - 1) / kMassRegThreads);
+  k<<<grid, kMassRegThreads, smem, st>>>(kp, U, static_cast<const float*>(Rin), static_cast<float*>(Rout),
+                                         static_cast<float*>(dU), Uout);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 }  // namespace dgcns

@@ -590,3 +590,27 @@ def test_mixed_face_centric_L_and_stage_random_states(k, periodic):
     inc = (Uo.cpu() - U)
     l2, mx = rel_err(inc, ork.B[3] * dUg.double().cpu())
     assert l2 < 1e-10 and mx < 1e-10, (l2, mx)
+
+
+@pytest.mark.parametrize("stage", [0, 3])
+def test_mixed_split_stage_and_inverse_mass_in_place(stage):
+    """Mixed form, split organisation (its M^-1 + stage kernel keeps every cell-component block in registers
+    at k = 3): one RK stage on random states of a ragged 5x3x4 box against the oracle (dU to FP32 accuracy,
+    U_out - U = B dU at FP64 rounding), and M^-1 in place (in == out) against the oracle's LU solve."""
+    g, op = pair((5, 3, 4), 3, precision=1, kernel=0)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 27)
+    dU0 = inputs.uniform(U.shape, 28)
+    dt = 1e-3
+    dUg, Uo = on_gpu(dU0).float().contiguous(), g.empty_state()
+    g.rk_stage(stage, dt, 0.0, on_gpu(U), dUg, Uo)
+    g.status()
+    dU_ref = ork.A[stage] * dU0.float().double() + dt * op.L(U)
+    l2, mx = rel_err(dUg, dU_ref)
+    assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
+    l2, mx = rel_err(Uo.cpu() - U, ork.B[stage] * dUg.double().cpu())
+    assert l2 < 1e-10 and mx < 1e-10, (l2, mx)
+    R = inputs.uniform(U.shape, 29).float()
+    Rg = on_gpu(R).float().contiguous()
+    g.inverse_mass(Rg, Rg)
+    l2, mx = rel_err(Rg, op.mass_solve(R.double()))
+    assert l2 < 1e-5 and mx < 1e-4, (l2, mx)
