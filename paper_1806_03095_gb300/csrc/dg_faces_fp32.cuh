@@ -48,6 +48,28 @@ __device__ __forceinline__ void eo_apply(const float* __restrict__ E, const floa
   }
 }
 
+// K consecutive floats between registers and memory: 16-byte vectors when K is a multiple of 4 (the
+// address then 16-byte aligned), else scalars.
+template <int K>
+__device__ __forceinline__ void arr_load(const float* p, float (&x)[K]) {
+  if constexpr (K % 4 == 0) {
+    vec_load<float, K>(p, x);
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) x[i] = p[i];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void arr_store(float* p, const float (&x)[K]) {
+  if constexpr (K % 4 == 0) {
+    vec_store<float, K>(p, x);
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) p[i] = x[i];
+  }
+}
+
 // 2D tensor contraction in registers: X[NI1][NI0] (index 0 fastest) -> Y[NO1][NO0] with operator E0 along
 // index 0 and E1 along index 1 (either may be the identity: NI == NO and E == nullptr is not used; every
 // call applies both).
@@ -219,13 +241,13 @@ __device__ __forceinline__ void face_task_body(const KParams& kp, float* __restr
       float Uv[PV], G[PV];
       float* o = fb + S::CIN + (sd * 5 + c) * S::VS;
       eo_2d<N, N, QV, QV, 1, 1>(tb.eSv, tb.eSv, L, Uv);
-      vec_store<float, PV>(o, Uv);
+      arr_store<PV>(o, Uv);
       eo_dir0<QV, QV, QV, -1>(tb.eDv, Uv, G);
-      vec_store<float, PV>(o + PV, G);
+      arr_store<PV>(o + PV, G);
       eo_dir1<QV, QV, QV, -1>(tb.eDv, Uv, G);
-      vec_store<float, PV>(o + 2 * PV, G);
+      arr_store<PV>(o + 2 * PV, G);
       eo_2d<N, N, QV, QV, 1, 1>(tb.eSv, tb.eSv, D, G);
-      vec_store<float, PV>(o + 3 * PV, G);
+      arr_store<PV>(o + 3 * PV, G);
     }
   }
   __syncthreads();
@@ -367,27 +389,27 @@ __device__ __forceinline__ void face_task_body(const KParams& kp, float* __restr
     if (kp.visc) {
       const float* vi = fb + S::CIN + (sd * 5 + c) * S::VS;
       float V[PV], G[PV], T[PV], Y[N2];
-      vec_load<float, PV>(vi, V);
-      vec_load<float, PV>(vi + PV, G);
+      arr_load<PV>(vi, V);
+      arr_load<PV>(vi + PV, G);
       eo_dir0<QV, QV, QV, -1>(tb.eDvT, G, T);
 #pragma unroll
       for (int p = 0; p < PV; ++p) V[p] += T[p];
-      vec_load<float, PV>(vi + 2 * PV, G);
+      arr_load<PV>(vi + 2 * PV, G);
       eo_dir1<QV, QV, QV, -1>(tb.eDvT, G, T);
 #pragma unroll
       for (int p = 0; p < PV; ++p) V[p] += T[p];
       eo_2d<QV, QV, N, N, 1, 1>(tb.eSvT, tb.eSvT, V, Y);
 #pragma unroll
       for (int j = 0; j < N2; ++j) Ls[j] += Y[j];
-      vec_load<float, PV>(vi + 3 * PV, G);
+      arr_load<PV>(vi + 3 * PV, G);
       eo_2d<QV, QV, N, N, 1, 1>(tb.eSvT, tb.eSvT, G, Y);
 #pragma unroll
       for (int j = 0; j < N2; ++j) Ds[j] = Y[j];
     }
     const int f = 2 * d + (sd ? 1 - s : s);
     float* po = FB + (((size_t)cell * 6 + f) * 2 * 5 + c) * N2;
-    vec_store<float, N2>(po, Ls);
-    vec_store<float, N2>(po + 5 * N2, Ds);
+    arr_store<N2>(po, Ls);
+    arr_store<N2>(po + 5 * N2, Ds);
   }
 }
 
@@ -456,15 +478,23 @@ __global__ void __launch_bounds__(NTH) dg_face_task_kernel(const KParams kp, flo
     face_task_body<N, QC, QV, FPB, NTH, 2>(kp, FB, tb, ph, sface, stau, eo, en, nb, s);
 }
 
-// The task kernel serves the FP32 affine face terms at k = 3 (the register arrays of larger k spill).
+// The task kernel serves the FP32 affine face terms at k = 3.  It compiles without spills at k = 4 and 5
+// (128 and 255 registers per thread), but there it was slower than the warp-per-face kernel (mixed TGV per
+// stage: k = 4, 51^3: 2.00 against 1.68 ms; k = 5, 40^3: 1.66 against 1.30 ms; measured): fewer warps fit
+// an SM.  Faces per CTA by degree, for the shared memory of larger faces.
 template <int N, int QC, int QV>
 constexpr bool task_faces_ok() {
-  return N == 4 && (QV * QV) % 4 == 0 && (N * N) % 4 == 0;
+  return N == 4;
+}
+
+template <int N>
+constexpr int task_faces_per_cta() {
+  return N == 4 ? 12 : (N == 5 ? 8 : 6);
 }
 
 template <int N, int QC, int QV>
 int launch_task_faces(const KParams& kp, void* FB, cudaStream_t st) {
-  constexpr int FPB = 12, NTH = 128;
+  constexpr int FPB = task_faces_per_cta<N>(), NTH = 128;
   constexpr size_t smem = task_face_smem_bytes<N, QC, QV, FPB>();
   static_assert(smem <= 227 * 1024, "task face kernel shared memory");
   int extra_items = 0;

@@ -548,12 +548,13 @@ def test_lsrk_stage_and_steps_general_2n_schemes():
 
 @pytest.mark.parametrize("what", ["F", "FC", "FV"])
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
-@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_mixed_face_centric_random_states(k, periodic, what):
     """The mixed form's face-centric kernels (FP32 arithmetic) on random states: independent nodal draws give
     jumps on every face and no cancellation between the weak-form terms, so F, F_c and F_v agree with the
     FP64 oracle to FP32 accuracy (2-norm 1e-5, max 1e-4 relative).  A ragged 3x4x5 box, periodic or with
-    walls on all six sides (lower and upper wall faces of every direction)."""
+    walls on all six sides (lower and upper wall faces of every direction); k = 3, 4, 5 (the FP32 task face
+    kernel at every degree, the task cell kernel at k = 3)."""
     lo, hi = (-1.0, -1.5, -2.0), (2.0, 1.5, 2.5)
     g, op = pair((3, 4, 5), k, precision=1, kernel=2, periodic=periodic, lo=lo, hi=hi)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 23)
@@ -566,7 +567,7 @@ def test_mixed_face_centric_random_states(k, periodic, what):
 
 
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
-@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_mixed_face_centric_L_and_stage_random_states(k, periodic):
     """The mixed form's face-centric cell + inverse-mass + stage kernel on random states against the FP64
     oracle: L(U) to FP32 accuracy (2-norm 1e-5, max 1e-4 relative), and one RK stage (stage 3: dU is read):
