@@ -375,6 +375,7 @@ def extras(args, cfg):
     torch.cuda.empty_cache()
     res["adjoint"], res["adjoint_element_centric"], res["adjoint_mixed"] = adjoint_extras()
     res.update(other_workloads(steps))
+    res["rotated_frames"] = rotated_frames(steps)
     res["mixed_dissipation_history"] = dissipation_history()
     res["memory_bound_kernels"] = memory_bound_kernels()
     res["k_sweep"] = k_sweep()
@@ -412,6 +413,31 @@ def other_workloads(steps):
                                            "rel_max": float(d.abs().max() / L64.abs().max())}
     del g64, g32, U, L64, d
     torch.cuda.empty_cache()
+    return out
+
+
+def rotated_frames(steps):
+    """Rotated-frame meshes (every cell in one of the 48 cube frames, neighbours read through per-face
+    orientation codes) against the same box with aligned frames, affine and deformed, all with geometry on
+    the fly: TGV 48^3, k = 3, the element-centric kernels in FP64 and in the mixed form."""
+    from paper_1806_03095_gb300 import api, configs
+    device = torch.cuda.current_device()
+    out = {"workload": "TGV 48^3, k = 3, geometry on the fly; rotated: frames seeded 1806, aligned: the same "
+                       "box through the same kernels with every frame the identity; deformed: the sine "
+                       "deformation of amplitude 0.05 on top"}
+    base = dict(configs.WORKLOADS["tgv48_k3"](), geometry=1)
+    meshes = (("rotated", api.MAP_ROTATED, 1806.0, 0.0), ("aligned", api.MAP_SINE, 0.0, 0.0),
+              ("rotated_deformed", api.MAP_ROTATED, 1806.0, 0.05), ("aligned_deformed", api.MAP_SINE, 0.05, 0.0))
+    for prec in (0, 1):
+        for kn, kv in (("fused", 1), ("split", 0)):
+            for frames, mapping, param, deform in meshes:
+                cfg = dict(base, precision=prec, kernel=kv, mapping=mapping, map_param=param, deform=deform)
+                ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+                key = "%s_%s_%s" % ("fp64" if prec == 0 else "mixed", kn, frames)
+                out[key] = {"value": _rate(ms, bufs[0].numel() // 5, steps), "unit": UNIT,
+                            "ms_per_step": round(ms / steps, 3)}
+                del ctx, bufs
+                torch.cuda.empty_cache()
     return out
 
 

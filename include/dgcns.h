@@ -65,6 +65,19 @@ extern "C" {
 #define DGCNS_MAP_AFFINE 0   /* uniform Cartesian box (Sec. 4.2.1)                     */
 #define DGCNS_MAP_CHANNEL 1  /* y -> tanh(C(2 eta - 1))/tanh(C), C = map_param (Sec. 4.3.1) */
 #define DGCNS_MAP_SINE 2     /* smooth periodic deformation of amplitude map_param    */
+/* Periodic affine box whose cells carry their own reference frames, as the cells of an unstructured
+ * hexahedral mesh do (Sec. 4.1.1: meshes that are not Cartesian-aligned).  Cell e's frame is one of the
+ * 48 symmetries of the cube, g = floor(48 u_e) with u_e the uniform of element e of Philox4x32-10 with
+ * key = (uint64) map_param (as dg_cns_set_initial_channel draws them): permutation
+ * P[g / 8] of {(0,1,2), (0,2,1), (1,0,2), (1,2,0), (2,0,1), (2,1,0)} and reflection bits g % 8.  A local
+ * reference point xi of the cell lies at the box reference point eta with
+ * eta_a = xi_{P[a]} (bit a of g clear) or 1 - xi_{P[a]} (set), so neighbouring cells see each other's
+ * face nodes permuted and reflected.  With deform != 0 the node coordinates are then moved by
+ * DGCNS_MAP_SINE's deformation of amplitude deform (curved cells with arbitrary relative orientations:
+ * the deformed unstructured mesh of Sec. 4.1.1).  Requires all axes periodic, geometry DGCNS_GEO_ON_THE_FLY and
+ * the split or fused kernel (the element-centric face terms reorient each neighbour into the cell's
+ * frame); the adjoint calls return UNSUPPORTED. */
+#define DGCNS_MAP_ROTATED 3
 
 #define DGCNS_OP_L 0  /* L(U) = M^-1 (-F(U) + F_rhs(U))        */
 #define DGCNS_OP_F 1  /* F(U) = F_c(U) + F_v(U)  (no mass matrix) */
@@ -83,7 +96,9 @@ typedef struct {
   double lo[3], hi[3];
   int periodic[3];
   int mapping;      /* DGCNS_MAP_* ; the geometry is isoparametric of degree k */
-  double map_param; /* channel stretch C, or sine amplitude (fraction of the box length) */
+  double map_param; /* channel stretch C, sine amplitude (fraction of the box length), or frame seed */
+  double deform;    /* DGCNS_MAP_ROTATED: amplitude of DGCNS_MAP_SINE's deformation applied to the box
+                       on top of the frames (0: affine cells); must be 0 for the other mappings */
 } dgcns_mesh;
 
 /* Discretisation and physics.  mu = rho0 U0 L / Re, lambda = mu c_p / Pr,

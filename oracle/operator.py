@@ -163,6 +163,8 @@ class DGOperator:
 
     def _exterior(self, U, E, d, s, nq, Um):
         """Exterior trace: neighbour cell's values/gradients at the shared points, or the wall state."""
+        if getattr(self.mesh, "frames", None) is not None:
+            return self._exterior_located(U, E, d, s, nq)
         nb = self.nbr[E, d, s]
         interior = nb >= 0
         nb_safe = torch.where(interior, nb, E)
@@ -176,6 +178,29 @@ class DGOperator:
             mask = interior[:, None, None]
             Up = torch.where(mask, Up, ghost)
         return Up, Gp, interior, nb_safe
+
+    def _exterior_located(self, U, E, d, s, nq):
+        """Rotated-frame meshes: the neighbour's polynomial and its physical gradient at the physical positions
+        of this cell's face points, located in the neighbour's own reference frame (periodic boxes, no walls).
+        A face point is located through its box coordinates.  On deformed meshes this finds the same physical
+        point because both cells interpolate the same deformation at the same face nodes, so their degree-k
+        geometries have the same trace on the shared face."""
+        m = self.mesh
+        En = E.numpy()
+        nb = self.nbr[E, d, s]
+        pts, _ = face_points(nq, d, s)
+        eta = m.to_box(En, pts) - m.offset[En, d, s][:, None, :]  # box coordinates in the neighbour's box
+        zeta = m.from_box(nb.numpy(), eta)  # [len(E), P, 3] in the neighbour's frame
+        phi, grad = basis_3d(m.nodes_1d, zeta.reshape(-1, 3))
+        P, n3 = pts.shape[0], m.n ** 3
+        phi = _t(phi).reshape(len(E), P, n3)
+        grad = _t(grad).reshape(len(E), P, n3, 3)
+        Un = U[nb]
+        Up = torch.einsum("epn,ecn->epc", phi, Un)
+        Jinv = torch.linalg.inv(torch.einsum("ean,epnb->epab", self.xyz[nb], grad))
+        gxi = torch.einsum("epnb,ecn->epcb", grad, Un)
+        Gp = torch.einsum("epba,epcb->epca", Jinv, gxi)
+        return Up, Gp, torch.ones(len(E), dtype=torch.bool), nb
 
     def _face_chunk(self, U, E, d, s, what):
         g, phys = self.phys.gamma, self.phys

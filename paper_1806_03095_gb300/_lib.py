@@ -14,7 +14,7 @@ ERR_NAMES = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "OOM", -5: "N
 
 FP64, MIXED = 0, 1
 KERNEL_SPLIT, KERNEL_FUSED, KERNEL_FACES = 0, 1, 2
-MAP_AFFINE, MAP_CHANNEL, MAP_SINE = 0, 1, 2
+MAP_AFFINE, MAP_CHANNEL, MAP_SINE, MAP_ROTATED = 0, 1, 2, 3
 GEO_STORED, GEO_ON_THE_FLY = 0, 1
 OP_L, OP_F, OP_FC, OP_FV = 0, 1, 2, 3
 NDIAG = 9
@@ -37,7 +37,8 @@ KERNEL_KINDS = ("cell", "face", "mass", "fused", "faces", "cell_stage", "dev", "
 
 class Mesh(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("periodic", ctypes.c_int * 3), ("mapping", ctypes.c_int), ("map_param", ctypes.c_double)]
+                ("periodic", ctypes.c_int * 3), ("mapping", ctypes.c_int), ("map_param", ctypes.c_double),
+                ("deform", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):

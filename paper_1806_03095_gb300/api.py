@@ -12,11 +12,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (FP64, KERNEL_FACES, KERNEL_FUSED, KERNEL_SPLIT, MAP_AFFINE, MAP_CHANNEL, MAP_SINE, MIXED, NDIAG,
+from ._lib import (FP64, KERNEL_FACES, KERNEL_FUSED, KERNEL_SPLIT, MAP_AFFINE, MAP_CHANNEL, MAP_ROTATED, MAP_SINE,
+                   MIXED, NDIAG,
                    OP_F, OP_FC, OP_FV, OP_L, DGCNSError)
 
 __all__ = ["DGCNS", "DGCNSError", "FP64", "MIXED", "KERNEL_SPLIT", "KERNEL_FUSED", "KERNEL_FACES", "OP_L", "OP_F",
-           "OP_FC", "OP_FV", "MAP_AFFINE", "MAP_CHANNEL", "MAP_SINE", "NDIAG"]
+           "OP_FC", "OP_FV", "MAP_AFFINE", "MAP_CHANNEL", "MAP_SINE", "MAP_ROTATED", "NDIAG"]
 
 
 def _ptr(t):
@@ -41,7 +42,8 @@ class DGCNS:
 
     def __init__(self, ncells, lo, hi, periodic, k, nq_conv, nq_visc, *, gamma=1.4, Pr=0.71, Re=1600.0,
                  Ma=0.1, R=287.0, rho0=1.0, U0=1.0, L=1.0, u_mach=0.0, body_force=(0.0, 0.0, 0.0),
-                 precision=FP64, kernel=KERNEL_FACES, mapping=MAP_AFFINE, map_param=0.0, geometry=0, device=None):
+                 precision=FP64, kernel=KERNEL_FACES, mapping=MAP_AFFINE, map_param=0.0, deform=0.0, geometry=0,
+                 device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libdgcns needs a CUDA device (there is no CPU fallback)")
         self.lib = _lib.load()
@@ -56,6 +58,7 @@ class DGCNS:
             p.body_force[d] = float(body_force[d])
         m.mapping = int(mapping)
         m.map_param = float(map_param)
+        m.deform = float(deform)
         p.k, p.nq_conv, p.nq_visc = int(k), int(nq_conv), int(nq_visc)
         p.gamma, p.Pr, p.Re, p.Ma, p.R = float(gamma), float(Pr), float(Re), float(Ma), float(R)
         p.rho0, p.U0, p.L, p.u_mach = float(rho0), float(U0), float(L), float(u_mach)

@@ -46,7 +46,8 @@ def make_context(cfg, device=None):
     return DGCNS(cfg["ncells"], cfg["lo"], cfg["hi"], cfg["periodic"], cfg["k"], cfg["nq_conv"], cfg["nq_visc"],
                  gamma=cfg["gamma"], Pr=cfg["Pr"], Re=cfg["Re"], Ma=cfg["Ma"], R=cfg["R"], u_mach=cfg["u_mach"],
                  body_force=cfg["body_force"], precision=cfg["precision"], kernel=cfg["kernel"],
-                 mapping=cfg["mapping"], map_param=cfg["map_param"], geometry=cfg.get("geometry", 0), device=device)
+                 mapping=cfg["mapping"], map_param=cfg["map_param"], deform=cfg.get("deform", 0.0),
+                 geometry=cfg.get("geometry", 0), device=device)
 
 
 def time_step(cfg, h_min=None):

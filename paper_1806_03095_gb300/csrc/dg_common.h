@@ -94,6 +94,9 @@ struct KParams {
   void* devOut;
   // Device error word of the context: kernels with bounded waits set it to 1 when a wait gives up.
   int* err;
+  // Rotated-frame meshes (DGCNS_MAP_ROTATED): per cell and local face [Nc][6][2] the neighbour cell and the
+  // orientation code of its frame relative to the cell's (frame_node); nullptr on structured meshes.
+  const int* fnbr;
   KConst<double> cd;
   KConst<float> cf;
 };
@@ -118,6 +121,22 @@ void fill_kconst(const KParams& kp, KConst<T>& c) {
 }
 
 constexpr int GEO_AFFINE = 0, GEO_STORED = 1, GEO_FLY = 2;
+
+// Node index, in its own frame, of the neighbour's node that sits at node q = (i0, i1, i2) of the
+// neighbour seen in the cell's frame: j_b = i_{src_b} or N - 1 - i_{src_b} (code bits: src_b at 2b, the
+// reflection of axis b at 6 + b).
+template <int N>
+__host__ __device__ __forceinline__ int frame_node(int code, int q) {
+  const int i0 = q % N, i1 = (q / N) % N, i2 = q / (N * N);
+  int j[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int src = (code >> (2 * b)) & 3;
+    const int v = src == 0 ? i0 : (src == 1 ? i1 : i2);
+    j[b] = ((code >> (6 + b)) & 1) ? N - 1 - v : v;
+  }
+  return j[0] + N * (j[1] + N * j[2]);
+}
 
 // Dynamic shared-memory attribute of a kernel: a per-device setting, made once per (kernel, device) on
 // the current device.  done[] is the kernel's own flag array (a static of its launcher).

@@ -189,24 +189,37 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
             else
               w = 1;
           }
-          const int en = w ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+          // rotated-frame meshes: the neighbour across the local face from the face table
+          const int en = kp.fnbr ? kp.fnbr[((size_t)e * 6 + 2 * d + s) * 2]
+                                 : (w ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]));
           nbi[threadIdx.x] = en;
           wall[threadIdx.x] = w;
           const double te = kp.tau[e];
           tau_f[threadIdx.x] = T(w ? te : fmax(te, kp.tau[en]));
         }
         __syncthreads();
+        // the neighbour's block, on rotated-frame meshes reoriented into this cell's frame
         for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
           const int e = i / (5 * N3);
           if (!wall[e]) {
-            const size_t src = (size_t)nbi[e] * 5 * N3 + (i - e * 5 * N3);
+            int r = i - e * 5 * N3;
+            if (kp.fnbr) {
+              const int cq = r / N3;
+              r = cq * N3 + frame_node<N>(kp.fnbr[((size_t)(e0 + e) * 6 + 2 * d + s) * 2 + 1], r - cq * N3);
+            }
+            const size_t src = (size_t)nbi[e] * 5 * N3 + r;
             sn[i] = Ud ? Ud[src] : T(U[src] - ref_of(kp, (i / N3) % 5));
           }
         }
         if (GEO == GEO_FLY) {
           for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) {
             const int e = i / (3 * N3);
-            sxn[i] = wall[e] ? sx[i] : static_cast<const T*>(kp.xyzT)[(size_t)nbi[e] * 3 * N3 + (i - e * 3 * N3)];
+            int r = i - e * 3 * N3;
+            if (kp.fnbr) {
+              const int cq = r / N3;
+              r = cq * N3 + frame_node<N>(kp.fnbr[((size_t)(e0 + e) * 6 + 2 * d + s) * 2 + 1], r - cq * N3);
+            }
+            sxn[i] = wall[e] ? sx[i] : static_cast<const T*>(kp.xyzT)[(size_t)nbi[e] * 3 * N3 + r];
           }
         }
         __syncthreads();
@@ -805,7 +818,8 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
             else
               wl = 1;
           }
-          const int en = wl ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]);
+          const int en = kp.fnbr ? kp.fnbr[((size_t)e0 * 6 + 2 * d + s) * 2]
+                                 : (wl ? -1 : c[0] + kp.nc[0] * (c[1] + kp.nc[1] * c[2]));
           nbi[0] = en;
           wall[0] = wl;
           const double te = kp.tau[e0];
@@ -813,12 +827,20 @@ __global__ void __launch_bounds__(WPC * 32) dg_op_warp_kernel(const KParams kp, 
         }
         grp.sync();
         if (!wall[0]) {
+          // the neighbour's block, on rotated-frame meshes reoriented into this cell's frame
           const size_t nb0 = (size_t)nbi[0] * 5 * N3;
-          for (int i = grp.rank(); i < nvals; i += 32)
-            sn[i] = Ud ? Ud[nb0 + i] : T(U[nb0 + i] - ref_of(kp, (i / N3) % 5));
+          const int code = kp.fnbr ? kp.fnbr[((size_t)e0 * 6 + 2 * d + s) * 2 + 1] : 0;
+          for (int i = grp.rank(); i < nvals; i += 32) {
+            const int cq = i / N3;
+            const int r = kp.fnbr ? cq * N3 + frame_node<N>(code, i - cq * N3) : i;
+            sn[i] = Ud ? Ud[nb0 + r] : T(U[nb0 + r] - ref_of(kp, cq % 5));
+          }
           if (GEO == GEO_FLY) {
             const T* Xn = static_cast<const T*>(kp.xyzT) + (size_t)nbi[0] * 3 * N3;
-            for (int i = grp.rank(); i < 3 * N3; i += 32) sxn[i] = Xn[i];
+            for (int i = grp.rank(); i < 3 * N3; i += 32) {
+              const int cq = i / N3;
+              sxn[i] = Xn[kp.fnbr ? cq * N3 + frame_node<N>(code, i - cq * N3) : i];
+            }
           }
         } else if (GEO == GEO_FLY) {
           for (int i = grp.rank(); i < 3 * N3; i += 32) sxn[i] = sx[i];

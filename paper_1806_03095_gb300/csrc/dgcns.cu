@@ -269,6 +269,7 @@ struct dgcns_ctx {
   size_t gsize[5] = {0, 0, 0, 0, 0};
   double* d_partial = nullptr;
   int* d_err = nullptr;  // error word of the kernels with bounded waits
+  int* d_fnbr = nullptr;  // rotated-frame meshes: neighbour and orientation per local face
   int diag_blocks = 0;
   int64_t launches = 0;
   // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
@@ -336,19 +337,104 @@ static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 
 static size_t state_bytes(const dgcns_ctx* c) { return c->state_elems * sizeof(double); }
 
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, each
+// multiplying words 0 and 2 by the round multipliers, mixing the high halves with words 1 and 3 and
+// the key, permuting; the key advances by the Weyl increments between rounds.
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Uniform in [0, 1) for element i: block i / 2 (counter (i / 2, 0, 0, 0), key = seed), words (0, 1) for
+// even i, (2, 3) for odd i, 53 bits as (a >> 5) 2^26 + (b >> 6).
+__host__ __device__ __forceinline__ double philox_u01(uint64_t i, uint64_t seed) {
+  const uint64_t j = i >> 1;
+  uint32_t c[4] = {(uint32_t)j, (uint32_t)(j >> 32), 0u, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t a = (i & 1) ? c[2] : c[0], b = (i & 1) ? c[3] : c[1];
+  const uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+  return (double)k * 0x1.0p-53;
+}
+
+
+// Frames of DGCNS_MAP_ROTATED: g in [0, 48), permutation kFramePerm[g / 8], reflection bits g % 8; a local
+// reference point xi lies at eta_a = xi_{P[a]} (bit a clear) or 1 - xi_{P[a]} (set) of the cell's box.
+static const int kFramePerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+static std::vector<int> cell_frames(const dgcns_mesh& m) {
+  const long long Nc = (long long)m.n[0] * m.n[1] * m.n[2];
+  std::vector<int> g((size_t)Nc, 0);
+  if (m.mapping != DGCNS_MAP_ROTATED) return g;
+  const uint64_t seed = (uint64_t)m.map_param;
+  for (long long e = 0; e < Nc; ++e) {
+    const int v = (int)(philox_u01((uint64_t)e, seed) * 48.0);
+    g[(size_t)e] = v > 47 ? 47 : v;
+  }
+  return g;
+}
+
+// Local axis of frame g that lies along box axis a, and whether it is reflected.
+static int frame_axis(int g, int a) { return kFramePerm[g / 8][a]; }
+static bool frame_flip(int g, int a) { return ((g % 8) >> a) & 1; }
+
+// Per cell e and local face f = 2 d + s: the neighbour cell across it and the orientation code of that
+// neighbour relative to e's frame, [Nc][6][2].  The code maps the node index (i0, i1, i2) of the
+// neighbour seen in e's frame to its own node index: j_b = i_{src_b}, or N - 1 - i_{src_b} when bit 6 + b
+// is set, with src_b in bits 2b..2b+1 (the composition of e's frame with the inverse of n's).  Periodic
+// boxes only.
+static std::vector<int> frame_face_table(const dgcns_mesh& m, const std::vector<int>& frames) {
+  const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+  const long long Nc = (long long)nx * ny * nz;
+  std::vector<int> t((size_t)Nc * 12);
+  for (long long e = 0; e < Nc; ++e) {
+    const int cc[3] = {(int)(e % nx), (int)((e / nx) % ny), (int)(e / ((long long)nx * ny))};
+    const int ge = frames[(size_t)e];
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        int A = 0;
+        while (frame_axis(ge, A) != d) ++A;
+        const int S = frame_flip(ge, A) ? 1 - s : s;  // the face's side along box axis A
+        int c2[3] = {cc[0], cc[1], cc[2]};
+        c2[A] = (c2[A] + (S ? 1 : -1) + m.n[A]) % m.n[A];
+        const long long n = c2[0] + (long long)nx * (c2[1] + (long long)ny * c2[2]);
+        const int gn = frames[(size_t)n];
+        int code = 0;
+        for (int a = 0; a < 3; ++a) {
+          const int b = frame_axis(gn, a), src = frame_axis(ge, a);
+          code |= src << (2 * b);
+          if (frame_flip(ge, a) != frame_flip(gn, a)) code |= 1 << (6 + b);
+        }
+        t[((size_t)e * 6 + 2 * d + s) * 2] = (int)n;
+        t[((size_t)e * 6 + 2 * d + s) * 2 + 1] = code;
+      }
+  }
+  return t;
+}
+
 static void map_point(const dgcns_mesh& m, double* x) {
   const double L[3] = {m.hi[0] - m.lo[0], m.hi[1] - m.lo[1], m.hi[2] - m.lo[2]};
   if (m.mapping == DGCNS_MAP_CHANNEL) {
     const double C = m.map_param;
     const double eta = (x[1] - m.lo[1]) / L[1];
     x[1] = 0.5 * (m.lo[1] + m.hi[1]) + 0.5 * L[1] * std::tanh(C * (2.0 * eta - 1.0)) / std::tanh(C);
-  } else if (m.mapping == DGCNS_MAP_SINE) {
+  } else if (m.mapping == DGCNS_MAP_SINE || (m.mapping == DGCNS_MAP_ROTATED && m.deform != 0.0)) {
+    const double A = m.mapping == DGCNS_MAP_SINE ? m.map_param : m.deform;
     double X[3], disp[3];
     for (int b = 0; b < 3; ++b) X[b] = (x[b] - m.lo[b]) / L[b];
     for (int a = 0; a < 3; ++a) {
       double s = 1.0;
       for (int b = 0; b < 3; ++b) s *= std::sin(2.0 * M_PI * X[b] + 0.5 * a * (b + 1));
-      disp[a] = m.map_param * L[a] * s;
+      disp[a] = A * L[a] * s;
     }
     for (int a = 0; a < 3; ++a) x[a] += disp[a];
   }
@@ -369,12 +455,19 @@ std::vector<double> host_node_coords(const dgcns_mesh& m, int k) {
   for (int d = 0; d < 3; ++d) h[d] = (m.hi[d] - m.lo[d]) / m.n[d];
   const long long Nc = (long long)m.n[0] * m.n[1] * m.n[2];
   std::vector<double> host((size_t)Nc * 3 * N3);
+  const std::vector<int> frames = cell_frames(m);
   for (long long e = 0; e < Nc; ++e) {
     const int cc[3] = {(int)(e % m.n[0]), (int)((e / m.n[0]) % m.n[1]), (int)(e / ((long long)m.n[0] * m.n[1]))};
+    const int g = frames[(size_t)e];
     for (int i = 0; i < N3; ++i) {
       const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
       double x[3];
-      for (int d = 0; d < 3; ++d) x[d] = m.lo[d] + (cc[d] + nodes[ii[d]]) * h[d];
+      for (int d = 0; d < 3; ++d) {
+        // the node's position along box axis d: local axis frame_axis(g, d), reflected or not (the LGL
+        // nodes are symmetric: node N-1-i sits at 1 - xi_i)
+        const int li = ii[frame_axis(g, d)];
+        x[d] = m.lo[d] + (cc[d] + nodes[frame_flip(g, d) ? N - 1 - li : li]) * h[d];
+      }
       map_point(m, x);
       for (int d = 0; d < 3; ++d) host[((size_t)e * 3 + d) * N3 + i] = x[d];
     }
@@ -387,34 +480,6 @@ std::vector<double> host_node_coords(const dgcns_mesh& m, int k) {
 // ---------------------------------------------------------------------------
 // Initial states (dg_cns_set_initial_tgv / dg_cns_set_initial_channel)
 // ---------------------------------------------------------------------------
-// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, each
-// multiplying words 0 and 2 by the round multipliers, mixing the high halves with words 1 and 3 and
-// the key, permuting; the key advances by the Weyl increments between rounds.
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
-
-// Uniform in [0, 1) for element i: block i / 2 (counter (i / 2, 0, 0, 0), key = seed), words (0, 1) for
-// even i, (2, 3) for odd i, 53 bits as (a >> 5) 2^26 + (b >> 6).
-__device__ __forceinline__ double philox_u01(uint64_t i, uint64_t seed) {
-  const uint64_t j = i >> 1;
-  uint32_t c[4] = {(uint32_t)j, (uint32_t)(j >> 32), 0u, 0u};
-  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-  const uint32_t a = (i & 1) ? c[2] : c[0], b = (i & 1) ? c[3] : c[1];
-  const uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
-  return (double)k * 0x1.0p-53;
-}
-
 // Channel start (Sec. 4.3.1): rho = rho0, u1 = u_max (1 - y^2) + a p1, u2 = a p2, u3 = a p3 with
 // a = 5 % u_max and p in [-1, 1) from Philox (element (cell 3 + component) n^3 + node); rho E =
 // rho0 (c_v T0 + |u|^2 / 2).  Every operation explicitly rounded, in a fixed order, so that the result
@@ -497,8 +562,22 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     return bad(DGCNS_ERR_INVALID_ARG, "geometry must be DGCNS_GEO_STORED or DGCNS_GEO_ON_THE_FLY");
   if (prm->kernel != DGCNS_KERNEL_SPLIT && prm->kernel != DGCNS_KERNEL_FUSED && prm->kernel != DGCNS_KERNEL_FACES)
     return bad(DGCNS_ERR_INVALID_ARG, "kernel must be DGCNS_KERNEL_SPLIT, DGCNS_KERNEL_FUSED or DGCNS_KERNEL_FACES");
-  if (mesh->mapping != DGCNS_MAP_AFFINE && mesh->mapping != DGCNS_MAP_CHANNEL && mesh->mapping != DGCNS_MAP_SINE)
+  if (mesh->mapping != DGCNS_MAP_AFFINE && mesh->mapping != DGCNS_MAP_CHANNEL && mesh->mapping != DGCNS_MAP_SINE &&
+      mesh->mapping != DGCNS_MAP_ROTATED)
     return bad(DGCNS_ERR_INVALID_ARG, "unknown mapping");
+  if (mesh->mapping == DGCNS_MAP_ROTATED) {
+    if (!mesh->periodic[0] || !mesh->periodic[1] || !mesh->periodic[2])
+      return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes must be periodic on every axis");
+    if (prm->geometry != DGCNS_GEO_ON_THE_FLY)
+      return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes need geometry on the fly");
+    if (prm->kernel == DGCNS_KERNEL_FACES)
+      return bad(DGCNS_ERR_UNSUPPORTED, "rotated-frame meshes run the split or fused (element-centric) kernels");
+    if (!(mesh->map_param >= 0.0 && mesh->map_param < 18446744073709551616.0) ||
+        mesh->map_param != std::floor(mesh->map_param))
+      return bad(DGCNS_ERR_INVALID_ARG, "the frame seed (map_param) must be a non-negative integer below 2^64");
+  }
+  if (mesh->mapping == DGCNS_MAP_ROTATED ? !std::isfinite(mesh->deform) : mesh->deform != 0.0)
+    return bad(DGCNS_ERR_INVALID_ARG, "deform must be finite, and 0 unless the mapping is DGCNS_MAP_ROTATED");
   if (mesh->mapping == DGCNS_MAP_CHANNEL && !(mesh->map_param > 0.0))
     return bad(DGCNS_ERR_INVALID_ARG, "channel stretch factor must be positive");
   // checked factor by factor, so that the product cannot overflow before the comparison
@@ -687,6 +766,13 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     }
   }
   kp.xyzT = c->d_xyz;  // the operator kernels recompute the Jacobians when set
+  if (mesh->mapping == DGCNS_MAP_ROTATED) {
+    const std::vector<int> ft = frame_face_table(*mesh, cell_frames(*mesh));
+    if (cudaMalloc(&c->d_fnbr, ft.size() * sizeof(int)) != cudaSuccess) return create_fail(c, "face table");
+    if (cudaMemcpy(c->d_fnbr, ft.data(), ft.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return create_fail(c, "face table upload");
+    kp.fnbr = c->d_fnbr;
+  }
   // diagnostics partial sums
   KParams kd = kp;
   kd.tables = c->d_tab64;
@@ -731,6 +817,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFree(c->d_partial);
   cudaFree(c->d_err);
+  cudaFree(c->d_fnbr);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
     cudaFree(c->g32[i]);
@@ -1091,6 +1178,7 @@ int dg_cns_adjoint_apply(dgcns_ctx* c, const double* U, const void* W, void* G) 
   if (!c) return DGCNS_ERR_INVALID_ARG;
   DeviceScope ds(c);
   if (!U || !W || !G) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
+  if (c->kp.fnbr) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint on rotated-frame meshes is not implemented");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
   if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
   if (overlap(G, res_bytes(c), U, state_bytes(c))) return fail(c, DGCNS_ERR_INVALID_ARG, "G must not overlap U");
@@ -1110,6 +1198,7 @@ int dg_cns_rk_stage_adjoint(dgcns_ctx* c, int stage, double dt, const double* U_
   if (stage < 0 || stage > 4) return fail(c, DGCNS_ERR_INVALID_ARG, "stage must be 0..4");
   if (!U_in || !lam_U || !lam_dU) return fail(c, DGCNS_ERR_INVALID_ARG, "NULL array");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DGCNS_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (c->kp.fnbr) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint on rotated-frame meshes is not implemented");
   if (c->kp.has_bf) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint with a body force is not implemented");
   if (!(c->L.features & FEAT_ADJ)) return fail(c, DGCNS_ERR_UNSUPPORTED, "adjoint not compiled for this (k, nq)");
   if (overlap(lam_U, state_bytes(c), U_in, state_bytes(c)) || overlap(lam_dU, res_bytes(c), U_in, state_bytes(c)) ||

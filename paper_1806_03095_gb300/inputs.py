@@ -58,6 +58,14 @@ def philox_uniform(n, seed):
     return torch.from_numpy(k.astype(np.float64) * 2.0 ** -53)
 
 
+def cell_frames(n_cells, seed):
+    """Reference frames of a rotated-frame box mesh: frame e = min(floor(48 u_e), 47) with u_e the e-th Philox
+    uniform of the seed (frame g: the (g // 8)-th permutation of the axes in lexicographic order, reflection
+    bits g % 8)."""
+    u = philox_uniform(n_cells, seed).numpy()
+    return np.minimum(np.floor(48.0 * u), 47).astype(np.int64)
+
+
 def _gen(seed):
     g = torch.Generator(device="cpu")
     g.manual_seed(int(seed))

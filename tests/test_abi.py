@@ -107,7 +107,7 @@ def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
     m, p = _lib.Mesh(), _lib.Params()
     for d in range(3):
         m.n[d], m.lo[d], m.hi[d], m.periodic[d] = 2, 0.0, 1.0, 1
-    m.mapping, m.map_param = mapping, (1.8 if mapping == 1 else 0.05)
+    m.mapping, m.map_param = mapping, {1: 1.8, 3: 1806.0}.get(mapping, 0.05)
     if mapping == 1:
         m.periodic[1], m.lo[1] = 0, -1.0
     p.k, p.nq_conv, p.nq_visc = k, qc, qv
@@ -126,6 +126,9 @@ def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
     (dict(k=3, qc=5, qv=4, kernel=3), -1),               # unknown kernel organisation
     (dict(k=3, qc=5, qv=4, geometry=2), -1),             # unknown geometry mode
     (dict(k=3, qc=5, qv=4, precision=2), -1),            # unknown precision
+    (dict(k=3, qc=5, qv=4, mapping=3, geometry=0), -1),  # rotated frames need geometry on the fly
+    (dict(k=3, qc=5, qv=4, mapping=3, geometry=1, kernel=2), -2),  # and the element-centric kernels
+    (dict(k=2, qc=4, qv=3, mapping=3, geometry=1, kernel=1), -2),  # geometry on the fly only at k = 3
 ])
 def test_create_rejects_uncompiled_or_invalid_features_on_host(lib, case, code):
     """The feature table of the instantiations answers before any device work."""
@@ -178,3 +181,21 @@ def test_kernel_kinds_match_header():
 
 def test_library_is_in_tree():
     assert os.path.dirname(LIB) == os.path.join(ROOT, "paper_1806_03095_gb300")
+
+
+@pytest.mark.parametrize("change,message", [
+    (lambda m: m.periodic.__setitem__(2, 0), b"rotated-frame meshes must be periodic on every axis"),
+    (lambda m: setattr(m, "map_param", -1.0), b"the frame seed (map_param) must be a non-negative integer below 2^64"),
+    (lambda m: setattr(m, "map_param", 2.5), b"the frame seed (map_param) must be a non-negative integer below 2^64"),
+    (lambda m: setattr(m, "map_param", 2.0 ** 64), b"the frame seed (map_param) must be a non-negative integer below 2^64"),
+    (lambda m: setattr(m, "deform", float("nan")), b"deform must be finite, and 0 unless the mapping is DGCNS_MAP_ROTATED"),
+    (lambda m: (setattr(m, "mapping", 2), setattr(m, "deform", 0.05)),
+     b"deform must be finite, and 0 unless the mapping is DGCNS_MAP_ROTATED"),
+])
+def test_create_validates_rotated_frame_meshes_on_host(lib, change, message):
+    m, p = _mesh_params(3, 5, 4, kernel=1, mapping=3, geometry=1)
+    change(m)
+    ctx = ctypes.c_void_p()
+    assert lib.dg_cns_create(ctypes.byref(m), ctypes.byref(p), None, ctypes.byref(ctx)) == -1
+    assert ctx.value is None
+    assert lib.dg_cns_last_error(None) == message

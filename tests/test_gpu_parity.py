@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from oracle import diagnostics as odiag, physics as ph, rk as ork
-from oracle.mesh import BoxMesh
+from oracle.mesh import BoxMesh, RotatedBoxMesh
 from oracle.operator import WHAT_ALL, WHAT_CONV, WHAT_VISC, DGOperator
 from paper_1806_03095_gb300 import inputs
 
@@ -487,6 +487,76 @@ def test_channel_geometry_on_the_fly_mixed_error(kernel):
     U = inputs.channel_state(op.xyz, 1806)
     l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
     assert l2 < 1e-3 and mx < 1e-2, (l2, mx)
+
+
+# -- rotated-frame meshes: every cell in one of the 48 cube frames, neighbours read through orientation codes --
+ROT_LO, ROT_HI = (-1.0, 0.0, 0.5), (2.0, 1.5, 2.5)
+
+
+def pair_rotated(ncells, seed, precision=0, kernel=1, deform=0.0):
+    k, qc, qv = 3, 5, 4
+    g = DGCNS(ncells, ROT_LO, ROT_HI, (1, 1, 1), k, qc, qv, precision=precision, kernel=kernel,
+              mapping=api.MAP_ROTATED, map_param=float(seed), deform=deform, geometry=1)
+    mesh = RotatedBoxMesh(ncells, ROT_LO, ROT_HI, k, inputs.cell_frames(int(np.prod(ncells)), seed), deform=deform)
+    return g, DGOperator(mesh, ph.Physics.from_numbers(1600.0, 0.71, 0.1), qc, qv)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("ncells,seed,deform", [((3, 2, 4), 1806, 0.0), ((4, 3, 3), (1 << 40) + 3, 0.0),
+                                                ((3, 3, 2), 99, 0.06)])
+def test_rotated_frame_mesh_fp64(ncells, seed, deform, kernel):
+    """Split and fused element-centric kernels on a periodic box whose cells have random frames, affine or
+    moved by the sine deformation: node coordinates, the TGV initial state, F_c, F_v, L(U) on a random state
+    (FP64, 1e-12) and one RK(5,4) step against the oracle, which locates the neighbour's polynomial at the
+    physical face points."""
+    g, op = pair_rotated(ncells, seed, kernel=kernel, deform=deform)
+    xyz = g.node_coords().cpu()
+    assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
+    l2, mx = rel_err(g.set_initial_tgv().cpu(), inputs.tgv_state(op.xyz))
+    assert l2 < 1e-14 and mx < 1e-14, (l2, mx)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 91)
+    for what, code in ((WHAT_CONV, api.OP_FC), (WHAT_VISC, api.OP_FV)):
+        l2, mx = rel_err(g.apply(on_gpu(U), op=code), op.residual(U, what))
+        assert l2 < TOL64 and mx < TOL64, (what, l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    dt = 1e-3
+    Ug = on_gpu(U)
+    g.rk_steps(1, dt, 0.0, Ug)
+    Ur = ork.step(lambda V, t: op.L(V), U, dt, 0.0)
+    l2, mx = rel_err(Ug - on_gpu(U), Ur - U)
+    assert l2 < 1e-9 and mx < 1e-9, (l2, mx)
+
+
+@pytest.mark.parametrize("deform", [0.0, 0.06])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_rotated_frame_mesh_mixed(kernel, deform):
+    """The mixed form on the rotated-frame box: F and L(U) of a random state to FP32 accuracy."""
+    g, op = pair_rotated((3, 4, 3), 7, precision=1, kernel=kernel, deform=deform)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 92)
+    for code, ref in ((api.OP_F, op.residual(U)), (api.OP_L, op.L(U))):
+        l2, mx = rel_err(g.apply(on_gpu(U), op=code), ref)
+        assert l2 < 1e-5 and mx < 1e-4, (code, l2, mx)
+
+
+def test_rotated_frame_mesh_is_not_the_aligned_mesh():
+    """The same state on the aligned box gives a different L: the frames are in effect."""
+    g, op = pair_rotated((3, 2, 4), 1806)
+    g0 = DGCNS((3, 2, 4), ROT_LO, ROT_HI, (1, 1, 1), 3, 5, 4, kernel=1, geometry=1, mapping=api.MAP_SINE,
+               map_param=0.0)
+    U = on_gpu(inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 91))
+    assert float((g.apply(U) - g0.apply(U)).abs().max()) > 1e-3 * float(g0.apply(U).abs().max())
+
+
+def test_rotated_frame_mesh_refusals():
+    g, _ = pair_rotated((2, 2, 2), 5)
+    U = g.set_initial_tgv()
+    with pytest.raises(api.DGCNSError) as ei:
+        g.adjoint_apply(U, U.clone())
+    assert ei.value.code == -2
+    with pytest.raises(api.DGCNSError) as ei:
+        pair_rotated((2, 2, 2), 5, kernel=2)
+    assert ei.value.code == -2
 
 
 def test_geometry_on_the_fly_unsupported_and_invalid():

@@ -11,8 +11,8 @@ import torch
 from torch.func import jvp, vmap
 
 from oracle import mms, physics as ph, rk
-from oracle.basis import basis_3d, cell_points, gauss_legendre_01, lagrange_1d
-from oracle.mesh import MAP_AFFINE, MAP_CHANNEL, MAP_SINE, BoxMesh
+from oracle.basis import basis_3d, cell_points, face_points, gauss_legendre_01, lagrange_1d
+from oracle.mesh import MAP_AFFINE, MAP_CHANNEL, MAP_SINE, BoxMesh, RotatedBoxMesh
 from oracle.operator import WHAT_ALL, WHAT_CONV, WHAT_VISC, DGOperator
 from paper_1806_03095_gb300 import inputs
 
@@ -483,3 +483,125 @@ def test_wall_ghost_state_negative_controls():
 
     assert not _wall_pins_hold(half_temperature)
     assert not _wall_pins_hold(first_component_only)
+
+
+# -- rotated-frame meshes ---------------------------------------------------------------------------------------
+ROT_NC, ROT_LO, ROT_HI = (3, 2, 4), (-1.0, 0.0, 0.5), (2.0, 1.5, 2.5)
+
+
+def _rotated_invariance_gap(mesh_cls=RotatedBoxMesh, op_cls=DGOperator, k=3, qc=5, qv=4, seed=1806, deform=0.0):
+    """Max-norm gap, relative to max |L|, between L on a rotated-frame box and L on the same box with aligned
+    frames (both moved by the same sine deformation), for a random discontinuous state carried node by node
+    into the rotated frames.  Nodes are matched by their physical coordinates.  Q_k and the tensor Gauss rules
+    are invariant under the 48 symmetries of the cube, the node set too, so both meshes interpolate the same
+    geometry; the weak form is written in physical space, so the two operators agree up to rounding."""
+    Nc = int(np.prod(ROT_NC))
+    m0 = BoxMesh(ROT_NC, ROT_LO, ROT_HI, (1, 1, 1), k, MAP_SINE, deform)
+    mr = mesh_cls(ROT_NC, ROT_LO, ROT_HI, k, inputs.cell_frames(Nc, seed), deform=deform)
+    dist = np.linalg.norm(mr.xyz[:, :, :, None] - m0.xyz[:, :, None, :], axis=1)  # [Nc, n^3 (rotated), n^3]
+    assert dist.min(2).max() < 1e-14
+    perm = torch.as_tensor(dist.argmin(2))
+    assert torch.equal(perm.sort(1).values, torch.arange(m0.n ** 3).expand(Nc, -1))
+    idx = perm[:, None, :].expand(-1, 5, -1)
+    phys = ph.Physics.from_numbers(1600.0, 0.71, 0.1)
+    U0 = inputs.random_state(Nc, m0.n ** 3, 3)
+    L0 = DGOperator(m0, phys, qc, qv).L(U0)
+    Lr = op_cls(mr, phys, qc, qv).L(torch.gather(U0, 2, idx))
+    return float((Lr - torch.gather(L0, 2, idx)).abs().max() / L0.abs().max())
+
+
+def test_rotated_frames_cover_reflections_and_cycles():
+    """The seeded frames of a 4096-cell mesh take all 48 values, so the pins below meet odd and even
+    permutations, 3-cycles and every reflection pattern."""
+    fr = inputs.cell_frames(4096, 1806)
+    assert set(fr.tolist()) == set(range(48))
+    mr = RotatedBoxMesh(ROT_NC, ROT_LO, ROT_HI, 3, inputs.cell_frames(24, 1806))
+    assert len(set((mr.frames // 8).tolist())) >= 4 and mr.flip.any(0).all()
+
+
+@pytest.mark.parametrize("k,qc,qv,deform", [(3, 5, 4, 0.0), (2, 3, 3, 0.0), (3, 5, 4, 0.05), (2, 4, 3, 0.08)])
+def test_rotated_frame_operator_invariance(k, qc, qv, deform):
+    assert _rotated_invariance_gap(k=k, qc=qc, qv=qv, deform=deform) < 1e-12
+
+
+def test_rotated_frame_located_points_are_physical_matches():
+    """On the deformed rotated-frame mesh, every located neighbour point maps (through the neighbour's own
+    degree-k geometry) to the physical position of the face point it stands for (through this cell's)."""
+    Nc = int(np.prod(ROT_NC))
+    mr = RotatedBoxMesh(ROT_NC, ROT_LO, ROT_HI, 3, inputs.cell_frames(Nc, 1806), deform=0.08)
+    E = np.arange(Nc)
+    L = mr.hi - mr.lo
+    for d in range(3):
+        for s in range(2):
+            pts, _ = face_points(5, d, s)
+            nb = mr.nbr[:, d, s]
+            zeta = mr.from_box(nb, mr.to_box(E, pts) - mr.offset[:, d, s][:, None, :])
+            x_own = np.einsum("pn,ean->epa", basis_3d(mr.nodes_1d, pts)[0], mr.xyz)
+            phi_n = basis_3d(mr.nodes_1d, zeta.reshape(-1, 3))[0].reshape(Nc, len(pts), -1)
+            x_nb = np.einsum("epn,ean->epa", phi_n, mr.xyz[nb])
+            gap = (x_nb - x_own) / L
+            gap -= np.round(gap)  # across the periodic boundary
+            assert np.abs(gap).max() < 1e-13, (d, s)
+
+
+def test_rotated_frame_neighbours_are_geometric():
+    """Every local face of every cell has a neighbour whose facing face coincides with it: the six face
+    centres of the neighbour contain this face's centre, and the relation is symmetric."""
+    Nc = int(np.prod(ROT_NC))
+    mr = RotatedBoxMesh(ROT_NC, ROT_LO, ROT_HI, 3, inputs.cell_frames(Nc, 1806))
+    E = np.arange(Nc)
+
+    def face_centres(cells):
+        out = []
+        for d in range(3):
+            for s in range(2):
+                c = np.full((1, 3), 0.5)
+                c[0, d] = float(s)
+                eta = mr.to_box(cells, c)[:, 0, :]
+                out.append((mr.cell_coords()[cells] + eta) % np.asarray(ROT_NC))
+        return np.stack(out, 1)  # [len(cells), 6, 3] box coordinates, wrapped
+
+    own = face_centres(E)
+    for d in range(3):
+        for s in range(2):
+            nb = mr.nbr[:, d, s]
+            theirs = face_centres(nb)
+            gap = np.abs(theirs - own[:, None, 2 * d + s, :])
+            gap = np.minimum(gap, np.asarray(ROT_NC) - gap).max(2)  # periodic distance
+            assert (gap.min(1) < 1e-12).all()
+            back = np.array([mr.nbr[n].reshape(-1) for n in nb])
+            assert (back == E[:, None]).any(1).all()
+
+
+class _NoReflection(RotatedBoxMesh):
+    """Planted mistake: neighbours located without their reflections."""
+    def from_box(self, E, eta):
+        E = np.asarray(E)
+        xi = np.empty_like(eta)
+        np.put_along_axis(xi, np.broadcast_to(self.perm[E][:, None, :], eta.shape), eta, axis=2)
+        return xi
+
+
+class _InversePermutation(RotatedBoxMesh):
+    """Planted mistake: the neighbour's axis permutation applied instead of its inverse."""
+    def from_box(self, E, eta):
+        E = np.asarray(E)
+        val = np.where(self.flip[E][:, None, :], 1.0 - eta, eta)
+        return np.take_along_axis(val, np.broadcast_to(self.perm[E][:, None, :], val.shape), axis=2)
+
+
+class _AlignedNeighbour(DGOperator):
+    """Planted mistake: the neighbour's trace taken on its own face (d, 1 - s) in this face's point order, as
+    on a mesh with aligned frames."""
+    def _exterior_located(self, U, E, d, s, nq):
+        nb = self.nbr[E, d, s]
+        phi, grad, _ = self.face_tables(nq, d, 1 - s)
+        Jinv = torch.linalg.inv(self.jacobian(self.xyz[nb], grad))
+        return self.values(phi, U[nb]), self.gradients(grad, Jinv, U[nb]), torch.ones(len(E), dtype=torch.bool), nb
+
+
+def test_rotated_frame_negative_controls():
+    assert _rotated_invariance_gap(mesh_cls=_NoReflection) > 1e-3
+    assert _rotated_invariance_gap(mesh_cls=_NoReflection, deform=0.05) > 1e-3
+    assert _rotated_invariance_gap(mesh_cls=_InversePermutation) > 1e-3
+    assert _rotated_invariance_gap(op_cls=_AlignedNeighbour) > 1e-3
