@@ -419,7 +419,7 @@ def other_workloads(steps):
 def rotated_frames(steps):
     """Rotated-frame meshes (every cell in one of the 48 cube frames, neighbours read through per-face
     orientation codes) against the same box with aligned frames, affine and deformed, all with geometry on
-    the fly: TGV 48^3, k = 3, the element-centric kernels in FP64 and in the mixed form."""
+    the fly: TGV 48^3, k = 3, the face-centric and element-centric kernels in FP64 and in the mixed form."""
     from paper_1806_03095_gb300 import api, configs
     device = torch.cuda.current_device()
     out = {"workload": "TGV 48^3, k = 3, geometry on the fly; rotated: frames seeded 1806, aligned: the same "
@@ -429,7 +429,7 @@ def rotated_frames(steps):
     meshes = (("rotated", api.MAP_ROTATED, 1806.0, 0.0), ("aligned", api.MAP_SINE, 0.0, 0.0),
               ("rotated_deformed", api.MAP_ROTATED, 1806.0, 0.05), ("aligned_deformed", api.MAP_SINE, 0.05, 0.0))
     for prec in (0, 1):
-        for kn, kv in (("fused", 1), ("split", 0)):
+        for kn, kv in (("faces", 2), ("fused", 1), ("split", 0)):
             for frames, mapping, param, deform in meshes:
                 cfg = dict(base, precision=prec, kernel=kv, mapping=mapping, map_param=param, deform=deform)
                 ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)

@@ -97,6 +97,10 @@ struct KParams {
   // Rotated-frame meshes (DGCNS_MAP_ROTATED): per cell and local face [Nc][6][2] the neighbour cell and the
   // orientation code of its frame relative to the cell's (frame_node); nullptr on structured meshes.
   const int* fnbr;
+  // Face-centric kernels on rotated-frame meshes: every face once, by the local face 2 d + s of the cell
+  // that owns it; flist + foff[2 d + s] holds flen[2 d + s] owner cells (nullptr: structured enumeration).
+  const int* flist;
+  int foff[6], flen[6];
   KConst<double> cd;
   KConst<float> cf;
 };
@@ -136,6 +140,15 @@ __host__ __device__ __forceinline__ int frame_node(int code, int q) {
     j[b] = ((code >> (6 + b)) & 1) ? N - 1 - v : v;
   }
   return j[0] + N * (j[1] + N * j[2]);
+}
+
+// The face of the neighbour that faces a cell across the cell's local face (d, s), seen through the
+// orientation code of frame_node: the neighbour's axis dn that the cell's axis d maps to, whether it is
+// reflected (then dV/dxi_d = -dV/dxi_dn), and the neighbour's side sn of that face.
+__host__ __device__ __forceinline__ void frame_facing(int code, int d, int s, int& dn, int& refl, int& sn) {
+  dn = ((code & 3) == d) ? 0 : (((code >> 2) & 3) == d ? 1 : 2);
+  refl = (code >> (6 + dn)) & 1;
+  sn = refl ? s : 1 - s;
 }
 
 // Dynamic shared-memory attribute of a kernel: a per-device setting, made once per (kernel, device) on

@@ -27,11 +27,16 @@ constexpr int fbuf_per_cell() {
 // lay: 4 trace layers [CB][5][N^2] (own values, own normal derivatives, other values, other normal
 // derivatives), read along the normal lines from global memory (the deviation state Ud when given,
 // else U - U_ref); lc: [CB][5][N^2] scratch; fa: face arena.
+// Rotated-frame meshes (oc != nullptr): the other cell is read through its orientation code oc[b] as if
+// it were aligned with the own cell, the face is evaluated in the own cell's frame, and the other cell's
+// shares go to the face and node positions of its own frame (frame_facing), its normal-derivative share
+// negated where its normal axis is reflected.
 template <typename T, int N, int QC, int QV, int CB, int d, int GEO, class G = CtaGroup>
 __device__ void face_pair_terms(const double* __restrict__ U, const T* __restrict__ Ud, const int* eo, const int* en,
                                 const T* tau_f, T* lay, T* fa, T* lc, const Tab<T>& tb, const KParams& kp,
                                 const PhysT<T>& ph, int nb, int s, T* __restrict__ FB, G grp = G(),
-                                const T* sx = nullptr, const T* sxn = nullptr, T* go = nullptr) {
+                                const T* sx = nullptr, const T* sxn = nullptr, T* go = nullptr,
+                                const int* oc = nullptr) {
   const int f = 2 * d + s, fo = 2 * d + (1 - s);
   constexpr int N2 = N * N, N3 = N * N * N;
   constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
@@ -71,7 +76,7 @@ __device__ void face_pair_terms(const double* __restrict__ U, const T* __restric
       T dq = T(0), vp = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const int q = face_node<N>(d, i, j1, j2);
+        const int q = oc ? frame_node<N>(oc[e], face_node<N>(d, i, j1, j2)) : face_node<N>(d, i, j1, j2);
         const T v = Ud ? Ud[op + q] : T(U[op + q] - dref);
         dq += dlp[i] * v;
         if (i == idp) vp = v;
@@ -314,9 +319,21 @@ __device__ void face_pair_terms(const double* __restrict__ U, const T* __restric
     po[0] = lc[idx] + lv;
     po[5 * N2] = dv;
     if (en[e] >= 0) {
-      T* pn = FB + ((size_t)en[e] * 6 + fo) * 10 * N2 + c * N2 + j;
+      int fw = fo, jw = j;
+      T dsg = T(1);
+      if (oc) {
+        // the other cell's face node of this face point, in its own frame
+        int dn, refl, sn;
+        frame_facing(oc[e], d, s, dn, refl, sn);
+        const int r = frame_node<N>(oc[e], face_node<N>(d, s ? 0 : N - 1, j % N, j / N));
+        const int r0 = r % N, r1 = (r / N) % N, r2 = r / (N * N);
+        fw = 2 * dn + sn;
+        jw = dn == 0 ? r1 + N * r2 : (dn == 1 ? r0 + N * r2 : r0 + N * r1);
+        dsg = refl ? T(-1) : T(1);
+      }
+      T* pn = FB + ((size_t)en[e] * 6 + fw) * 10 * N2 + c * N2 + jw;
       pn[0] = (kp.visc ? Lp[idx] : T(0)) - lc[idx];
-      pn[5 * N2] = kp.visc ? Dp[idx] : T(0);
+      pn[5 * N2] = kp.visc ? dsg * Dp[idx] : T(0);
     }
   }
 }

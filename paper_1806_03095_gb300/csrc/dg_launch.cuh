@@ -1010,7 +1010,7 @@ constexpr size_t face_smem_bytes() {
   const size_t geo = GEO == GEO_FLY ? (size_t)CB * (2 * 3 * S::N3 + S::FLY_OUT) : 0;
   const size_t elems = table_elems<N, QC, QV>() + (size_t)CB * PairSizes<N, QC, QV>::LAYERS +
                        (size_t)CB * 5 * S::N2 + face_arena_elems<T, N, QC, QV, CB, GEO>() + geo + CB;
-  return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
+  return elems * sizeof(T) + 3 * CB * sizeof(int) + 64;
 }
 
 // Faces per CTA: the largest batch (<= 8) below ~112 KB of shared memory.
@@ -1050,26 +1050,42 @@ __global__ void __launch_bounds__(face_threads<T, GEO>()) dg_face_kernel(const K
   T* tau_f = sx + (GEO == GEO_FLY ? CB * (2 * 3 * N3 + S::FLY_OUT) : 0);
   int* eo = reinterpret_cast<int*>(tau_f + CB);
   int* en = eo + CB;
+  int* oc = en + CB;  // rotated-frame meshes: orientation code of the other cell
 
   const int d = blockIdx.y;
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  const int nstd = (kp.Nc + CB - 1) / CB;
   int s, i0, nitems;
-  if ((int)blockIdx.x < nstd) {
-    s = 1;
-    i0 = blockIdx.x * CB;
-    nitems = kp.Nc;
-  } else {
-    if (kp.periodic[d]) return;
-    s = 0;
-    i0 = (blockIdx.x - nstd) * CB;
-    nitems = kp.nc[t1] * kp.nc[t2];
+  if (kp.flist) {  // rotated-frame meshes: the faces owned through local face (d, 1), then (d, 0)
+    const int nb1 = (kp.flen[2 * d + 1] + CB - 1) / CB;
+    s = (int)blockIdx.x < nb1 ? 1 : 0;
+    i0 = (s ? (int)blockIdx.x : (int)blockIdx.x - nb1) * CB;
+    nitems = kp.flen[2 * d + s];
     if (i0 >= nitems) return;
+  } else {
+    const int nstd = (kp.Nc + CB - 1) / CB;
+    if ((int)blockIdx.x < nstd) {
+      s = 1;
+      i0 = blockIdx.x * CB;
+      nitems = kp.Nc;
+    } else {
+      if (kp.periodic[d]) return;
+      s = 0;
+      i0 = (blockIdx.x - nstd) * CB;
+      nitems = kp.nc[t1] * kp.nc[t2];
+      if (i0 >= nitems) return;
+    }
   }
   const int nb = min(CB, nitems - i0);
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
   const PhysT<T> ph = make_phys<T>(kp);
-  if ((int)threadIdx.x < nb) {
+  if ((int)threadIdx.x < nb && kp.flist) {
+    const int e = kp.flist[kp.foff[2 * d + s] + i0 + threadIdx.x];
+    const int* t = kp.fnbr + ((size_t)e * 6 + 2 * d + s) * 2;
+    eo[threadIdx.x] = e;
+    en[threadIdx.x] = t[0];
+    oc[threadIdx.x] = t[1];
+    tau_f[threadIdx.x] = T(fmax(kp.tau[e], kp.tau[t[0]]));
+  } else if ((int)threadIdx.x < nb) {
     const int i = i0 + threadIdx.x;
     int c[3];
     if (s == 1) {
@@ -1098,22 +1114,29 @@ __global__ void __launch_bounds__(face_threads<T, GEO>()) dg_face_kernel(const K
   }
   __syncthreads();
   const T* Ud = static_cast<const T*>(kp.Udev);
+  const int* ocp = kp.flist ? oc : nullptr;
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT);
     for (int i = threadIdx.x; i < nb * 3 * N3; i += blockDim.x) {
       const int b = i / (3 * N3), r = i - b * 3 * N3;
       sx[i] = X[(size_t)eo[b] * 3 * N3 + r];
-      sxn[i] = X[(size_t)(en[b] >= 0 ? en[b] : eo[b]) * 3 * N3 + r];
+      // the other cell's coordinates, on rotated-frame meshes reoriented into the own cell's frame
+      const int cq = r / N3;
+      const int rn = ocp ? cq * N3 + frame_node<N>(ocp[b], r - cq * N3) : r;
+      sxn[i] = X[(size_t)(en[b] >= 0 ? en[b] : eo[b]) * 3 * N3 + rn];
     }
   }
   __syncthreads();
   const CtaGroup cg;
   if (d == 0)
-    face_pair_terms<T, N, QC, QV, CB, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go,
+                                              ocp);
   else if (d == 1)
-    face_pair_terms<T, N, QC, QV, CB, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go,
+                                              ocp);
   else
-    face_pair_terms<T, N, QC, QV, CB, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, CB, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, nb, s, FB, cg, sx, sxn, go,
+                                              ocp);
 }
 
 // Warp-per-face organisation of the same face kernel (used for the FP32 form, as the warp-per-cell
@@ -1146,17 +1169,24 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   const int w = threadIdx.x >> 5;
   const int d = blockIdx.y;
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  const int nstd = (kp.Nc + WPC - 1) / WPC;
   int s, i;
-  if ((int)blockIdx.x < nstd) {
-    s = 1;
-    i = blockIdx.x * WPC + w;
-    if (i >= kp.Nc) return;  // only warp barriers below
+  if (kp.flist) {  // rotated-frame meshes: the faces owned through local face (d, 1), then (d, 0)
+    const int nb1 = (kp.flen[2 * d + 1] + WPC - 1) / WPC;
+    s = (int)blockIdx.x < nb1 ? 1 : 0;
+    i = (s ? (int)blockIdx.x : (int)blockIdx.x - nb1) * WPC + w;
+    if (i >= kp.flen[2 * d + s]) return;  // only warp barriers below
   } else {
-    if (kp.periodic[d]) return;
-    s = 0;
-    i = (blockIdx.x - nstd) * WPC + w;
-    if (i >= kp.nc[t1] * kp.nc[t2]) return;
+    const int nstd = (kp.Nc + WPC - 1) / WPC;
+    if ((int)blockIdx.x < nstd) {
+      s = 1;
+      i = blockIdx.x * WPC + w;
+      if (i >= kp.Nc) return;  // only warp barriers below
+    } else {
+      if (kp.periodic[d]) return;
+      s = 0;
+      i = (blockIdx.x - nstd) * WPC + w;
+      if (i >= kp.nc[t1] * kp.nc[t2]) return;
+    }
   }
   const WarpGroup grp;
   T* lay = stab + table_elems<N, QC, QV>() + w * SL;
@@ -1166,10 +1196,18 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   T* sxn = sx + 3 * N3;
   T* go = sxn + 3 * N3;
   T* tau_f = sx + (GEO == GEO_FLY ? 2 * 3 * N3 + S::FLY_OUT : 0);
-  int* eo = reinterpret_cast<int*>(lay + SL) - 2;  // two ints at the end of the slice
+  int* eo = reinterpret_cast<int*>(lay + SL) - 3;  // three ints at the end of the slice
   int* en = eo + 1;
+  int* oc = eo + 2;  // rotated-frame meshes: orientation code of the other cell
   const PhysT<T> ph = make_phys<T>(kp);
-  if (grp.rank() == 0) {
+  if (grp.rank() == 0 && kp.flist) {
+    const int e = kp.flist[kp.foff[2 * d + s] + i];
+    const int* t = kp.fnbr + ((size_t)e * 6 + 2 * d + s) * 2;
+    eo[0] = e;
+    en[0] = t[0];
+    oc[0] = t[1];
+    tau_f[0] = T(fmax(kp.tau[e], kp.tau[t[0]]));
+  } else if (grp.rank() == 0) {
     int c[3];
     if (s == 1) {
       c[0] = i % kp.nc[0];
@@ -1197,20 +1235,27 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   }
   grp.sync();
   const T* Ud = static_cast<const T*>(kp.Udev);
+  const int* ocp = kp.flist ? oc : nullptr;
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT);
     for (int r = grp.rank(); r < 3 * N3; r += 32) {
       sx[r] = X[(size_t)eo[0] * 3 * N3 + r];
-      sxn[r] = X[(size_t)(en[0] >= 0 ? en[0] : eo[0]) * 3 * N3 + r];
+      // the other cell's coordinates, on rotated-frame meshes reoriented into the own cell's frame
+      const int cq = r / N3;
+      const int rn = ocp ? cq * N3 + frame_node<N>(ocp[0], r - cq * N3) : r;
+      sxn[r] = X[(size_t)(en[0] >= 0 ? en[0] : eo[0]) * 3 * N3 + rn];
     }
     grp.sync();
   }
   if (d == 0)
-    face_pair_terms<T, N, QC, QV, 1, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, 1, 0, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go,
+                                             ocp);
   else if (d == 1)
-    face_pair_terms<T, N, QC, QV, 1, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, 1, 1, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go,
+                                             ocp);
   else
-    face_pair_terms<T, N, QC, QV, 1, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go);
+    face_pair_terms<T, N, QC, QV, 1, 2, GEO>(U, Ud, eo, en, tau_f, lay, fa, lc, tb, kp, ph, 1, s, FB, grp, sx, sxn, go,
+                                             ocp);
 }
 
 template <typename T, int N, int QC, int QV, int GEO>
@@ -1222,8 +1267,17 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     if (plane > extra_items) extra_items = plane;
   }
   if constexpr (sizeof(T) == 4 && GEO == GEO_AFFINE && DGCNS_FP32_TASK_FACES && task_faces_ok<N, QC, QV>()) {
-    if (kp.Udev != nullptr) return launch_task_faces<N, QC, QV>(kp, FB, st);
+    if (kp.Udev != nullptr && kp.flist == nullptr) return launch_task_faces<N, QC, QV>(kp, FB, st);
   }
+  // rotated-frame meshes: per direction, the blocks of the (d, 1) list, then those of the (d, 0) list
+  auto list_blocks = [&](int per) {
+    int g = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int b = (kp.flen[2 * d + 1] + per - 1) / per + (kp.flen[2 * d] + per - 1) / per;
+      if (b > g) g = b;
+    }
+    return g;
+  };
   if constexpr (sizeof(T) == 4) {
     constexpr int WPC = 8;
     constexpr size_t smem = face_warp_smem_bytes<T, N, QC, QV, WPC, GEO>();
@@ -1231,7 +1285,7 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     auto k = dg_face_warp_kernel<T, N, QC, QV, WPC, GEO>;
     static bool attr[kMaxDevices] = {};
     if (smem_attr_once(k, smem, attr)) return -1;
-    const dim3 grid((kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
+    const dim3 grid(kp.flist ? list_blocks(WPC) : (kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
     k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<T*>(FB));
   } else {
     constexpr int CB = faces_per_cta<T, N, QC, QV, GEO>();
@@ -1240,7 +1294,7 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     auto k = dg_face_kernel<T, N, QC, QV, CB, GEO>;
     static bool attr[kMaxDevices] = {};
     if (smem_attr_once(k, smem, attr)) return -1;
-    const dim3 grid((kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
+    const dim3 grid(kp.flist ? list_blocks(CB) : (kp.Nc + CB - 1) / CB + (extra_items + CB - 1) / CB, 3);
     k<<<grid, face_threads<T, GEO>(), smem, st>>>(kp, U, static_cast<T*>(FB));
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -270,6 +270,7 @@ struct dgcns_ctx {
   double* d_partial = nullptr;
   int* d_err = nullptr;  // error word of the kernels with bounded waits
   int* d_fnbr = nullptr;  // rotated-frame meshes: neighbour and orientation per local face
+  int* d_flist = nullptr;  // rotated-frame meshes, face-centric kernels: faces by owner's local face
   int diag_blocks = 0;
   int64_t launches = 0;
   // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
@@ -421,6 +422,27 @@ static std::vector<int> frame_face_table(const dgcns_mesh& m, const std::vector<
   return t;
 }
 
+// Face lists of the face-centric kernels on rotated-frame meshes: every face once, owned by the cell whose
+// local upper face it is (the lower-indexed cell when it is an upper or a lower face of both), grouped by the
+// owner's local face f = 2 d + s; off[f] and len[f] locate group f.
+static std::vector<int> frame_face_lists(long long Nc, const std::vector<int>& t, int off[6], int len[6]) {
+  std::vector<std::vector<int>> groups(6);
+  for (long long e = 0; e < Nc; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int s = f & 1, n = t[((size_t)e * 6 + f) * 2], code = t[((size_t)e * 6 + f) * 2 + 1];
+      int dn, refl, sn;
+      frame_facing(code, f >> 1, s, dn, refl, sn);
+      if (s == 1 ? (sn == 0 || e < n) : (sn == 0 && e < n)) groups[f].push_back((int)e);
+    }
+  std::vector<int> out;
+  for (int f = 0; f < 6; ++f) {
+    off[f] = (int)out.size();
+    len[f] = (int)groups[f].size();
+    out.insert(out.end(), groups[f].begin(), groups[f].end());
+  }
+  return out;
+}
+
 static void map_point(const dgcns_mesh& m, double* x) {
   const double L[3] = {m.hi[0] - m.lo[0], m.hi[1] - m.lo[1], m.hi[2] - m.lo[2]};
   if (m.mapping == DGCNS_MAP_CHANNEL) {
@@ -570,8 +592,6 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
       return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes must be periodic on every axis");
     if (prm->geometry != DGCNS_GEO_ON_THE_FLY)
       return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes need geometry on the fly");
-    if (prm->kernel == DGCNS_KERNEL_FACES)
-      return bad(DGCNS_ERR_UNSUPPORTED, "rotated-frame meshes run the split or fused (element-centric) kernels");
     if (!(mesh->map_param >= 0.0 && mesh->map_param < 18446744073709551616.0) ||
         mesh->map_param != std::floor(mesh->map_param))
       return bad(DGCNS_ERR_INVALID_ARG, "the frame seed (map_param) must be a non-negative integer below 2^64");
@@ -772,6 +792,13 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     if (cudaMemcpy(c->d_fnbr, ft.data(), ft.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
       return create_fail(c, "face table upload");
     kp.fnbr = c->d_fnbr;
+    if (prm->kernel == DGCNS_KERNEL_FACES) {
+      const std::vector<int> fl = frame_face_lists(c->Nc, ft, kp.foff, kp.flen);
+      if (cudaMalloc(&c->d_flist, fl.size() * sizeof(int)) != cudaSuccess) return create_fail(c, "face lists");
+      if (cudaMemcpy(c->d_flist, fl.data(), fl.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return create_fail(c, "face list upload");
+      kp.flist = c->d_flist;
+    }
   }
   // diagnostics partial sums
   KParams kd = kp;
@@ -818,6 +845,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_partial);
   cudaFree(c->d_err);
   cudaFree(c->d_fnbr);
+  cudaFree(c->d_flist);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
     cudaFree(c->g32[i]);

@@ -501,14 +501,14 @@ def pair_rotated(ncells, seed, precision=0, kernel=1, deform=0.0):
     return g, DGOperator(mesh, ph.Physics.from_numbers(1600.0, 0.71, 0.1), qc, qv)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("ncells,seed,deform", [((3, 2, 4), 1806, 0.0), ((4, 3, 3), (1 << 40) + 3, 0.0),
-                                                ((3, 3, 2), 99, 0.06)])
+                                                ((3, 3, 2), 99, 0.06), ((1, 3, 2), 7, 0.04)])
 def test_rotated_frame_mesh_fp64(ncells, seed, deform, kernel):
-    """Split and fused element-centric kernels on a periodic box whose cells have random frames, affine or
-    moved by the sine deformation: node coordinates, the TGV initial state, F_c, F_v, L(U) on a random state
-    (FP64, 1e-12) and one RK(5,4) step against the oracle, which locates the neighbour's polynomial at the
-    physical face points."""
+    """Split, fused and face-centric kernels on a periodic box whose cells have random frames, affine or
+    moved by the sine deformation (one case with a single cell along x: a cell is its own neighbour): node
+    coordinates, the TGV initial state, F_c, F_v, L(U) on a random state (FP64, 1e-12) and one RK(5,4) step
+    against the oracle, which locates the neighbour's polynomial at the physical face points."""
     g, op = pair_rotated(ncells, seed, kernel=kernel, deform=deform)
     xyz = g.node_coords().cpu()
     assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
@@ -529,7 +529,7 @@ def test_rotated_frame_mesh_fp64(ncells, seed, deform, kernel):
 
 
 @pytest.mark.parametrize("deform", [0.0, 0.06])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_rotated_frame_mesh_mixed(kernel, deform):
     """The mixed form on the rotated-frame box: F and L(U) of a random state to FP32 accuracy."""
     g, op = pair_rotated((3, 4, 3), 7, precision=1, kernel=kernel, deform=deform)
@@ -548,14 +548,12 @@ def test_rotated_frame_mesh_is_not_the_aligned_mesh():
     assert float((g.apply(U) - g0.apply(U)).abs().max()) > 1e-3 * float(g0.apply(U).abs().max())
 
 
-def test_rotated_frame_mesh_refusals():
-    g, _ = pair_rotated((2, 2, 2), 5)
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_rotated_frame_mesh_refusals(kernel):
+    g, _ = pair_rotated((2, 2, 2), 5, kernel=kernel)
     U = g.set_initial_tgv()
     with pytest.raises(api.DGCNSError) as ei:
         g.adjoint_apply(U, U.clone())
-    assert ei.value.code == -2
-    with pytest.raises(api.DGCNSError) as ei:
-        pair_rotated((2, 2, 2), 5, kernel=2)
     assert ei.value.code == -2
 
 
