@@ -205,6 +205,12 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--kernel", choices=["fused", "split", "faces"], default="faces")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed/split comparison and CPU baseline")
+    ap.add_argument("--mesh", choices=["box", "rotated", "sine"], default="box",
+                    help="box: the workload's own mesh; rotated: every cell in a seeded cube frame (seed 1806); "
+                         "sine: the same box with aligned frames, deformed by --deform (both non-affine paths)")
+    ap.add_argument("--deform", type=float, default=0.0, help="sine deformation amplitude of --mesh rotated/sine")
+    ap.add_argument("--geometry", choices=["stored", "fly"], default="fly",
+                    help="geometry of --mesh rotated/sine: stored per point or recomputed in the kernels")
     ap.add_argument("--inverse-mass", action="store_true",
                     help="time dg_cns_inverse_mass alone on the workload (one JSON line; not the step metric)")
     ap.add_argument("--stability", action="store_true",
@@ -229,6 +235,13 @@ def main():
     torch.cuda.set_device(device)
     prec = 1 if args.precision == "mixed" else 0
     cfg = configs.WORKLOADS[args.workload](precision=prec, kernel=KERNELS[args.kernel])
+    mesh_note = ""
+    if args.mesh != "box":
+        cfg = dict(cfg, mapping=3 if args.mesh == "rotated" else 2,
+                   map_param=1806.0 if args.mesh == "rotated" else args.deform,
+                   deform=args.deform if args.mesh == "rotated" else 0.0,
+                   geometry=1 if args.geometry == "fly" else 0)
+        mesh_note = ", %s mesh (deform %g), geometry %s" % (args.mesh, args.deform, args.geometry)
     N = cfg["k"] + 1
     Nc = cfg["ncells"][0] * cfg["ncells"][1] * cfg["ncells"][2]
     nodes = Nc * N ** 3
@@ -247,8 +260,9 @@ def main():
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 arithmetic / f64 state", "data": "synthetic",
-           "config": {"workload": "Taylor-Green vortex %d^3 cells, k=%d, nq_conv=%d, nq_visc=%d, RK(5,4), %s, %s kernel"
-                      % (cfg["ncells"][0], cfg["k"], cfg["nq_conv"], cfg["nq_visc"], args.precision, args.kernel),
+           "config": {"workload": "Taylor-Green vortex %d^3 cells, k=%d, nq_conv=%d, nq_visc=%d, RK(5,4), %s, %s kernel%s"
+                      % (cfg["ncells"][0], cfg["k"], cfg["nq_conv"], cfg["nq_visc"], args.precision, args.kernel,
+                         mesh_note),
                       "cells": Nc, "nodes": nodes, "dofs": 5 * nodes,
                       "stages_timed": stages, "dt": dt,
                       "l2": "inputs larger than L2 (state %.0f MB per vector)" % (nodes * 40 / 1e6),
@@ -418,26 +432,32 @@ def other_workloads(steps):
 
 def rotated_frames(steps):
     """Rotated-frame meshes (every cell in one of the 48 cube frames, neighbours read through per-face
-    orientation codes) against the same box with aligned frames, affine and deformed, all with geometry on
-    the fly: TGV 48^3, k = 3, the face-centric and element-centric kernels in FP64 and in the mixed form."""
+    orientation codes) against the same box with aligned frames, affine and deformed: TGV 48^3, k = 3, FP64
+    and mixed; all three organisations with geometry on the fly, the face-centric one also with stored
+    geometry, and the Cartesian box (affine, no geometry arrays) for reference."""
     from paper_1806_03095_gb300 import api, configs
     device = torch.cuda.current_device()
-    out = {"workload": "TGV 48^3, k = 3, geometry on the fly; rotated: frames seeded 1806, aligned: the same "
-                       "box through the same kernels with every frame the identity; deformed: the sine "
-                       "deformation of amplitude 0.05 on top"}
-    base = dict(configs.WORKLOADS["tgv48_k3"](), geometry=1)
+    out = {"workload": "TGV 48^3, k = 3; rotated: frames seeded 1806, aligned: the same box through the same "
+                       "kernels with every frame the identity; deformed: the sine deformation of amplitude 0.05 "
+                       "on top; geometry on the fly, and stored geometry for the face-centric kernels; "
+                       "cartesian: the affine box without geometry arrays"}
+    base = configs.WORKLOADS["tgv48_k3"]()
     meshes = (("rotated", api.MAP_ROTATED, 1806.0, 0.0), ("aligned", api.MAP_SINE, 0.0, 0.0),
               ("rotated_deformed", api.MAP_ROTATED, 1806.0, 0.05), ("aligned_deformed", api.MAP_SINE, 0.05, 0.0))
-    for prec in (0, 1):
-        for kn, kv in (("faces", 2), ("fused", 1), ("split", 0)):
-            for frames, mapping, param, deform in meshes:
-                cfg = dict(base, precision=prec, kernel=kv, mapping=mapping, map_param=param, deform=deform)
-                ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
-                key = "%s_%s_%s" % ("fp64" if prec == 0 else "mixed", kn, frames)
-                out[key] = {"value": _rate(ms, bufs[0].numel() // 5, steps), "unit": UNIT,
-                            "ms_per_step": round(ms / steps, 3)}
-                del ctx, bufs
-                torch.cuda.empty_cache()
+    runs = [(prec, kn, kv, 1, m) for prec in (0, 1) for kn, kv in (("faces", 2), ("fused", 1), ("split", 0))
+            for m in meshes]
+    runs += [(prec, "faces", 2, 0, m) for prec in (0, 1) for m in meshes]
+    runs += [(prec, "faces", 2, 0, ("cartesian", api.MAP_AFFINE, 0.0, 0.0)) for prec in (0, 1)]
+    for prec, kn, kv, geo, (frames, mapping, param, deform) in runs:
+        cfg = dict(base, precision=prec, kernel=kv, mapping=mapping, map_param=param, deform=deform,
+                   geometry=geo)
+        ctx, bufs, dt, ms, _ = time_native(cfg, steps, 3, device)
+        key = "%s_%s_%s%s" % ("fp64" if prec == 0 else "mixed", kn, frames,
+                              "_stored" if geo == 0 and mapping != api.MAP_AFFINE else "")
+        out[key] = {"value": _rate(ms, bufs[0].numel() // 5, steps), "unit": UNIT,
+                    "ms_per_step": round(ms / steps, 3)}
+        del ctx, bufs
+        torch.cuda.empty_cache()
     return out
 
 

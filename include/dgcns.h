@@ -74,11 +74,11 @@ extern "C" {
  * eta_a = xi_{P[a]} (bit a of g clear) or 1 - xi_{P[a]} (set), so neighbouring cells see each other's
  * face nodes permuted and reflected.  With deform != 0 the node coordinates are then moved by
  * DGCNS_MAP_SINE's deformation of amplitude deform (curved cells with arbitrary relative orientations:
- * the deformed unstructured mesh of Sec. 4.1.1).  Requires all axes periodic and geometry
- * DGCNS_GEO_ON_THE_FLY.  The element-centric kernels reorient each neighbour into the cell's frame as they
- * read it; the face-centric face kernel evaluates each face in the frame of the cell that owns it (the
- * cell for which it is a local upper face) and writes the other cell's share into that cell's own face
- * slot and node order.  The adjoint calls return UNSUPPORTED. */
+ * the deformed unstructured mesh of Sec. 4.1.1).  Requires all axes periodic; stored geometry or geometry
+ * on the fly.  The element-centric kernels reorient each neighbour into the cell's frame as they read it
+ * (state, node coordinates, stored face Jacobians); the face-centric face kernel evaluates each face in the
+ * frame of the cell that owns it (the cell for which it is a local upper face) and writes the other cell's
+ * share into that cell's own face slot and node order.  The adjoint calls return UNSUPPORTED. */
 #define DGCNS_MAP_ROTATED 3
 
 #define DGCNS_OP_L 0  /* L(U) = M^-1 (-F(U) + F_rhs(U))        */

@@ -220,7 +220,9 @@ __device__ void face_pair_terms(const double* __restrict__ U, const T* __restric
         nrm[1] = g[10 * P];
         nrm[2] = g[11 * P];
         wgt = g[12 * P] * tb.wv[p % QV] * tb.wv[p / QV];
-        if (!wall) {
+        if (!wall && GEO == GEO_STORED && oc) {
+          frame_face_jinv<T, QV>(static_cast<const T*>(kp.gfv), en[e], oc[e], d, s, p, Jp);
+        } else if (!wall) {
           const T* gp = GEO == GEO_FLY ? gnb + (size_t)e * 13 * P + p
                                        : static_cast<const T*>(kp.gfv) + ((size_t)en[e] * 6 + fo) * 13 * P + p;
 #pragma unroll

@@ -360,6 +360,30 @@ __device__ __forceinline__ int face_node(int d, int id, int j1, int j2) {
   return j1 + N * (j2 + N * id);
 }
 
+// Rotated-frame meshes, stored geometry: the inverse Jacobian of the neighbour across a cell's local face
+// (d, s), at the point of the neighbour's own face that coincides with point p of the cell's Q x Q face
+// grid, with its rows re-expressed along the cell's reference axes (J^{-1}[b][a] = +-J_n^{-1}[b_n][a],
+// negative where the neighbour's axis b_n runs against the cell's axis b).  gf: the stored face geometry
+// [Nc][6][13][Q^2] (J^{-1} in entries 0..8, index 3 b + a); the Gauss points are symmetric about 1/2, so
+// a reflected coordinate index i is Q - 1 - i.
+template <typename T, int Q>
+__device__ __forceinline__ void frame_face_jinv(const T* __restrict__ gf, int nbr, int code, int d, int s, int p,
+                                                T Jp[9]) {
+  int dn, refl, sn;
+  frame_facing(code, d, s, dn, refl, sn);
+  const int r = frame_node<Q>(code, face_node<Q>(d, s ? 0 : Q - 1, p % Q, p / Q));
+  const int r0 = r % Q, r1 = (r / Q) % Q, r2 = r / (Q * Q);
+  const int pn = dn == 0 ? r1 + Q * r2 : (dn == 1 ? r0 + Q * r2 : r0 + Q * r1);
+  const T* g = gf + ((size_t)nbr * 6 + 2 * dn + sn) * 13 * Q * Q + pn;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int bn = (code & 3) == b ? 0 : (((code >> 2) & 3) == b ? 1 : 2);
+    const T sg = ((code >> (6 + bn)) & 1) ? T(-1) : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Jp[3 * b + a] = sg * g[(3 * bn + a) * Q * Q];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Geometry of the isoparametric map from the degree-k node coordinates X
 // ([CB][3][N^3]): interpolation to a point set and collocation derivatives
@@ -977,10 +1001,15 @@ __device__ void face_terms(const T* su, const T* sn, const int* wall, const int*
         wgt = g[12 * P] * tb.wv[p % QV] * tb.wv[p / QV];
         T Jp[9];
         if (!wall[e]) {
-          const T* gp = GEO == GEO_FLY ? gnb + (size_t)e * 13 * P + p
-                                       : static_cast<const T*>(kp.gfv) + ((size_t)nbi[e] * 6 + fo) * 13 * P + p;
+          if (GEO == GEO_STORED && kp.fnbr) {
+            frame_face_jinv<T, QV>(static_cast<const T*>(kp.gfv), nbi[e], kp.fnbr[((size_t)(e0 + e) * 6 + f) * 2 + 1],
+                                   d, s, p, Jp);
+          } else {
+            const T* gp = GEO == GEO_FLY ? gnb + (size_t)e * 13 * P + p
+                                         : static_cast<const T*>(kp.gfv) + ((size_t)nbi[e] * 6 + fo) * 13 * P + p;
 #pragma unroll
-          for (int m = 0; m < 9; ++m) Jp[m] = gp[m * P];
+            for (int m = 0; m < 9; ++m) Jp[m] = gp[m * P];
+          }
         } else {
 #pragma unroll
           for (int m = 0; m < 9; ++m) Jp[m] = Jm[m];

@@ -590,8 +590,6 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   if (mesh->mapping == DGCNS_MAP_ROTATED) {
     if (!mesh->periodic[0] || !mesh->periodic[1] || !mesh->periodic[2])
       return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes must be periodic on every axis");
-    if (prm->geometry != DGCNS_GEO_ON_THE_FLY)
-      return bad(DGCNS_ERR_INVALID_ARG, "rotated-frame meshes need geometry on the fly");
     if (!(mesh->map_param >= 0.0 && mesh->map_param < 18446744073709551616.0) ||
         mesh->map_param != std::floor(mesh->map_param))
       return bad(DGCNS_ERR_INVALID_ARG, "the frame seed (map_param) must be a non-negative integer below 2^64");

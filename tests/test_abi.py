@@ -126,7 +126,6 @@ def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
     (dict(k=3, qc=5, qv=4, kernel=3), -1),               # unknown kernel organisation
     (dict(k=3, qc=5, qv=4, geometry=2), -1),             # unknown geometry mode
     (dict(k=3, qc=5, qv=4, precision=2), -1),            # unknown precision
-    (dict(k=3, qc=5, qv=4, mapping=3, geometry=0), -1),  # rotated frames need geometry on the fly
     (dict(k=2, qc=4, qv=3, mapping=3, geometry=1, kernel=1), -2),  # geometry on the fly only at k = 3
 ])
 def test_create_rejects_uncompiled_or_invalid_features_on_host(lib, case, code):

@@ -493,23 +493,26 @@ def test_channel_geometry_on_the_fly_mixed_error(kernel):
 ROT_LO, ROT_HI = (-1.0, 0.0, 0.5), (2.0, 1.5, 2.5)
 
 
-def pair_rotated(ncells, seed, precision=0, kernel=1, deform=0.0):
+def pair_rotated(ncells, seed, precision=0, kernel=1, deform=0.0, geometry=1):
     k, qc, qv = 3, 5, 4
     g = DGCNS(ncells, ROT_LO, ROT_HI, (1, 1, 1), k, qc, qv, precision=precision, kernel=kernel,
-              mapping=api.MAP_ROTATED, map_param=float(seed), deform=deform, geometry=1)
+              mapping=api.MAP_ROTATED, map_param=float(seed), deform=deform, geometry=geometry)
     mesh = RotatedBoxMesh(ncells, ROT_LO, ROT_HI, k, inputs.cell_frames(int(np.prod(ncells)), seed), deform=deform)
     return g, DGOperator(mesh, ph.Physics.from_numbers(1600.0, 0.71, 0.1), qc, qv)
 
 
 @pytest.mark.parametrize("kernel", [0, 1, 2])
-@pytest.mark.parametrize("ncells,seed,deform", [((3, 2, 4), 1806, 0.0), ((4, 3, 3), (1 << 40) + 3, 0.0),
-                                                ((3, 3, 2), 99, 0.06), ((1, 3, 2), 7, 0.04)])
-def test_rotated_frame_mesh_fp64(ncells, seed, deform, kernel):
+@pytest.mark.parametrize("ncells,seed,deform,geometry", [((3, 2, 4), 1806, 0.0, 1), ((4, 3, 3), (1 << 40) + 3, 0.0, 1),
+                                                         ((3, 3, 2), 99, 0.06, 1), ((1, 3, 2), 7, 0.04, 1),
+                                                         ((3, 2, 4), 1806, 0.0, 0), ((3, 3, 2), 99, 0.06, 0),
+                                                         ((1, 3, 2), 7, 0.04, 0)])
+def test_rotated_frame_mesh_fp64(ncells, seed, deform, geometry, kernel):
     """Split, fused and face-centric kernels on a periodic box whose cells have random frames, affine or
-    moved by the sine deformation (one case with a single cell along x: a cell is its own neighbour): node
-    coordinates, the TGV initial state, F_c, F_v, L(U) on a random state (FP64, 1e-12) and one RK(5,4) step
-    against the oracle, which locates the neighbour's polynomial at the physical face points."""
-    g, op = pair_rotated(ncells, seed, kernel=kernel, deform=deform)
+    moved by the sine deformation (one case with a single cell along x: a cell is its own neighbour), with
+    geometry on the fly or stored (the neighbour's stored face Jacobians read through the orientation code):
+    node coordinates, the TGV initial state, F_c, F_v, L(U) on a random state (FP64, 1e-12) and one RK(5,4)
+    step against the oracle, which locates the neighbour's polynomial at the physical face points."""
+    g, op = pair_rotated(ncells, seed, kernel=kernel, deform=deform, geometry=geometry)
     xyz = g.node_coords().cpu()
     assert torch.allclose(xyz, op.xyz, rtol=0, atol=1e-14)
     l2, mx = rel_err(g.set_initial_tgv().cpu(), inputs.tgv_state(op.xyz))
@@ -528,11 +531,12 @@ def test_rotated_frame_mesh_fp64(ncells, seed, deform, kernel):
     assert l2 < 1e-9 and mx < 1e-9, (l2, mx)
 
 
+@pytest.mark.parametrize("geometry", [0, 1])
 @pytest.mark.parametrize("deform", [0.0, 0.06])
 @pytest.mark.parametrize("kernel", [0, 1, 2])
-def test_rotated_frame_mesh_mixed(kernel, deform):
+def test_rotated_frame_mesh_mixed(kernel, deform, geometry):
     """The mixed form on the rotated-frame box: F and L(U) of a random state to FP32 accuracy."""
-    g, op = pair_rotated((3, 4, 3), 7, precision=1, kernel=kernel, deform=deform)
+    g, op = pair_rotated((3, 4, 3), 7, precision=1, kernel=kernel, deform=deform, geometry=geometry)
     U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 92)
     for code, ref in ((api.OP_F, op.residual(U)), (api.OP_L, op.L(U))):
         l2, mx = rel_err(g.apply(on_gpu(U), op=code), ref)
