@@ -616,9 +616,10 @@ def inverse_mass_only(args):
 
 def k_sweep(steps=2):
     """Throughput against the polynomial degree (the paper's throughput-versus-k study, Sec. 4.1.2): TGV meshes
-    of about 84M DoFs for k = 2..7 (FP64; k = 3..5 also mixed), fused and face-centric kernels (k = 7:
-    face-centric only), and FP64 face-centric with the paper's 3/2 rule on both terms (k = 2..5) and the
-    2k+1 rule on both terms (k = 2..4)."""
+    of about 84M DoFs for k = 2..8, 11 and 15 (FP64; k = 3..5 also mixed), fused and face-centric kernels
+    (k >= 7: face-centric only; from k = 8 the cell kernel's working set in the global workspace), and FP64
+    face-centric with the paper's 3/2 rule on both terms (k = 2..5) and the 2k+1 rule on both terms
+    (k = 2..5, 7)."""
     from paper_1806_03095_gb300 import configs
     device = torch.cuda.current_device()
     out = {}
@@ -632,7 +633,7 @@ def k_sweep(steps=2):
         del ctx, bufs
         torch.cuda.empty_cache()
 
-    for k in (2, 3, 4, 5, 6, 7):
+    for k in (2, 3, 4, 5, 6, 7, 8, 11, 15):
         n = max(2, int(round((16.78e6 / (k + 1) ** 3) ** (1.0 / 3.0))))
         for prec in ((0, 1) if k in (3, 4, 5) else (0,)):
             for kern in ((1, 2) if k <= 6 else (2,)):
@@ -643,7 +644,7 @@ def k_sweep(steps=2):
             cfg = dict(configs.tgv(n, k, precision=0, kernel=2))
             cfg["nq_visc"] = cfg["nq_conv"]
             run("k%d_fp64_faces_3/2_rule_both_terms" % k, cfg)
-        if k <= 4:
+        if k <= 5 or k == 7:
             cfg = dict(configs.tgv(n, k, precision=0, kernel=2))
             cfg["nq_conv"] = cfg["nq_visc"] = 2 * k + 1
             run("k%d_fp64_faces_2k+1_rule_both_terms" % k, cfg)

@@ -107,7 +107,7 @@ typedef struct {
  * c_p = gamma R/(gamma-1), c0 = u_mach / Ma (u_mach = U0 when 0),
  * T0 = c0^2/(gamma R) (wall temperature), nu = mu / rho0 (Sec. 4.2.1, 4.3.1). */
 typedef struct {
-  int k;         /* polynomial degree, 1..6 in the shipped instantiations */
+  int k;         /* polynomial degree: 1..8, 11 and 15 in the shipped instantiations */
   int nq_conv;   /* Gauss points per direction for the convective terms   */
   int nq_visc;   /* Gauss points per direction for the viscous terms      */
   double gamma, Pr, Re, Ma, R, rho0, U0, L, u_mach;

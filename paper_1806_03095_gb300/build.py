@@ -84,6 +84,17 @@ def build(jobs=None, force=False, verbose=False, extra=()):
     host_obj = os.path.join(BUILD, "dgcns.o")
     cmds.append([exe, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, "dgcns.cu"), "-o", host_obj])
     objs.append(host_obj)
+
+    # longest translation units first (the operator and adjoint parts of the largest point sets), so that
+    # the wall time is not set by a long one started last
+    def cost(cmd):
+        d = dict(a[2:].split("=") for a in cmd if a.startswith("-DINST_"))
+        if not d:
+            return 1e6
+        q = int(d["INST_QC"]) ** 3 + int(d["INST_QV"]) ** 3
+        return q * {"0": 4, "1": 2, "3": 3, "4": 2, "6": 2}.get(d["INST_PART"], 1)
+
+    cmds.sort(key=cost, reverse=True)
     with cf.ThreadPoolExecutor(jobs) as ex:
         outs = list(ex.map(_run, cmds))
     if verbose:

@@ -101,6 +101,12 @@ struct KParams {
   // that owns it; flist + foff[2 d + s] holds flen[2 d + s] owner cells (nullptr: structured enumeration).
   const int* flist;
   int foff[6], flen[6];
+  // Operator kernels whose per-cell working set does not fit shared memory (high degrees): a global
+  // workspace of gws_elems values of the arithmetic type, one slice per CTA; the launcher runs the grid
+  // in chunks of as many CTAs as it holds, the first cell of a chunk in cell0 (0 otherwise).
+  void* gws;
+  size_t gws_elems;
+  int cell0;
   KConst<double> cd;
   KConst<float> cf;
 };

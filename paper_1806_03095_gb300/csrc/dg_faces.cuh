@@ -73,10 +73,18 @@ __device__ void face_pair_terms(const double* __restrict__ U, const T* __restric
       Dp[idx] = T(0);
     } else {
       const size_t op = ((size_t)en[e] * 5 + c) * N3;
+      // the normal line through face node j; on rotated-frame meshes it is a line of the other cell too,
+      // at a constant stride (+-1, +-N or +-N^2) from its reoriented first node
+      int q0 = face_node<N>(d, 0, j1, j2), qs = face_node<N>(d, 1, j1, j2) - q0;
+      if (oc) {
+        const int r0 = frame_node<N>(oc[e], q0);
+        qs = frame_node<N>(oc[e], q0 + qs) - r0;
+        q0 = r0;
+      }
       T dq = T(0), vp = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const int q = oc ? frame_node<N>(oc[e], face_node<N>(d, i, j1, j2)) : face_node<N>(d, i, j1, j2);
+        const int q = q0 + i * qs;
         const T v = Ud ? Ud[op + q] : T(U[op + q] - dref);
         dq += dlp[i] * v;
         if (i == idp) vp = v;

@@ -169,10 +169,14 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
   constexpr int NL = ISZ / DIN;
   constexpr int IST = AX == 0 ? 1 : (AX == 1 ? D0 : D0 * D1);
   constexpr int OST = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
-  const T* __restrict__ A = E;
-  const T* __restrict__ B = E + OH * IH;
-  const T* __restrict__ C = E + 2 * OH * IH;
   for (int l = grp.rank(); l < nblk * NL; l += grp.size()) {
+    // the operator table is loop-invariant; where it is large (high degrees) its loads stay inside the
+    // loop (the pointer passes through an empty asm), so that it is not hoisted into registers and spilled
+    const T* Ep = E;
+    if constexpr (2 * OH * IH > 48) asm volatile("" : "+l"(Ep));
+    const T* __restrict__ A = Ep;
+    const T* __restrict__ B = Ep + OH * IH;
+    const T* __restrict__ C = Ep + 2 * OH * IH;
     const int blk = l / NL, r = l - blk * NL;
     int ib, ob;
     if (AX == 0) {

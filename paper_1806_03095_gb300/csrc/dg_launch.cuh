@@ -96,6 +96,22 @@ constexpr size_t op_smem_bytes() {
   return elems * sizeof(T) + 2 * CB * sizeof(int) + 64;
 }
 
+// Per-CTA working set of the operator kernel (everything but the 1D tables), slices 256-byte aligned.
+// Where it does not fit shared memory next to the tables (at high degrees one cell's arena alone is
+// 15-20 q^3 values), it lives in the context's global workspace kp.gws instead, cached by L1 and L2.
+template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
+constexpr size_t op_work_elems() {
+  using S = Sizes<N, QC, QV>;
+  const size_t e = (size_t)CB * 5 * S::N3 * (FACE ? 3 : 2) + op_arena_elems<N, QC, QV, CB, CELL, FACE, MASS, GEO>() +
+                   op_geo_elems<N, QC, QV, CB, FACE, GEO>() + 4 * CB + 8;
+  return (e + 31) & ~(size_t)31;
+}
+
+template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool MASS, int GEO>
+constexpr bool op_gws() {
+  return op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>() > 227 * 1024;
+}
+
 // component c of the reference state U_ref = (rho_r, 0, 0, 0, rho_r c_v T_0)
 __device__ __forceinline__ double ref_of(const KParams& kp, int c) {
   return c == 0 ? kp.rho_ref : (c == 4 ? kp.rhoE_ref : 0.0);
@@ -116,6 +132,8 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* stab = sm;
   T* su = stab + table_elems<N, QC, QV>();
+  if constexpr (op_gws<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>())  // this CTA's slice of the global workspace
+    su = static_cast<T*>(kp.gws) + (size_t)blockIdx.x * op_work_elems<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
   T* sr = su + CB * 5 * N3;
   T* sn = sr + CB * 5 * N3;
   T* ar = sn + (FACE ? CB * 5 * N3 : 0);
@@ -126,7 +144,7 @@ __global__ void __launch_bounds__(op_threads<T>()) dg_op_kernel(const KParams kp
   int* wall = reinterpret_cast<int*>(tau_f + CB);
   int* nbi = wall + CB;
 
-  const int e0 = blockIdx.x * CB;
+  const int e0 = kp.cell0 + blockIdx.x * CB;
   const int nb = min(CB, kp.Nc - e0);
   if (nb <= 0) return;
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
@@ -712,14 +730,46 @@ template <typename T, int N, int QC, int QV, int CB, bool CELL, bool FACE, bool 
 int launch_op(const KParams& kp, const double* U, const void* Rin, void* Rout, void* dU, double* Uout,
               cudaStream_t st) {
   auto k = dg_op_kernel<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>;
-  constexpr size_t smem = op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
+  constexpr bool GWS = op_gws<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
+  constexpr size_t smem = GWS ? table_elems<N, QC, QV>() * sizeof(T) + 64
+                              : op_smem_bytes<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
   if (smem > 227 * 1024) return -2;
   static bool attr[kMaxDevices] = {};
   if (smem_attr_once(k, smem, attr)) return -1;
   const int grid = (kp.Nc + CB - 1) / CB;
-  k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout),
-                                          static_cast<T*>(dU), Uout);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  if constexpr (GWS) {
+    // global workspace: chunks of as many CTAs as it holds; returns the number of launches
+    constexpr size_t work = op_work_elems<T, N, QC, QV, CB, CELL, FACE, MASS, GEO>();
+    const int per = (int)(kp.gws ? kp.gws_elems / work : 0);
+    if (per < 1) return -2;
+    int launches = 0;
+    for (int b0 = 0; b0 < grid; b0 += per) {
+      KParams kc = kp;
+      kc.cell0 = b0 * CB;
+      k<<<min(per, grid - b0), op_threads<T>(), smem, st>>>(kc, U, static_cast<const T*>(Rin), static_cast<T*>(Rout),
+                                                            static_cast<T*>(dU), Uout);
+      if (cudaGetLastError() != cudaSuccess) return -1;
+      ++launches;
+    }
+    return launches;
+  } else {
+    k<<<grid, op_threads<T>(), smem, st>>>(kp, U, static_cast<const T*>(Rin), static_cast<T*>(Rout),
+                                            static_cast<T*>(dU), Uout);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  }
+}
+
+// Bytes per CTA of the global workspace that an (N, QC, QV) instantiation's CTA-wide operator kernels
+// need (0 when every variant fits shared memory): the largest over the variants with and without
+// element-centric faces.
+template <typename T, int N, int QC, int QV>
+constexpr size_t op_gws_bytes() {
+  constexpr int CB0 = cells_per_cta<T, N, QC, QV, false>(), CB1 = cells_per_cta<T, N, QC, QV, true>();
+  constexpr size_t a = op_gws<T, N, QC, QV, CB0, true, false, true, GEO_AFFINE>()
+                           ? op_work_elems<T, N, QC, QV, CB0, true, false, true, GEO_AFFINE>() * sizeof(T) : 0;
+  constexpr size_t b = op_gws<T, N, QC, QV, CB1, true, true, true, GEO_AFFINE>()
+                           ? op_work_elems<T, N, QC, QV, CB1, true, true, true, GEO_AFFINE>() * sizeof(T) : 0;
+  return a > b ? a : b;
 }
 
 // ---------------------------------------------------------------------------
@@ -910,7 +960,7 @@ int op_dispatch_geo(int mode, const KParams& kp, const double* U, const void* Ri
           return launch_mass_reg<N, QC, QV, false>(kp, Rin, Rout, dU, U, Uout, st);
         }
       }
-      if constexpr (mass_tma_ok<T, N>() && GEO != GEO_FLY) {
+      if constexpr (mass_tma_ok<T, N>() && GEO != GEO_FLY && mass_tma_bytes<T, N, QC, QV, true>(1) <= 227 * 1024) {
         // the TMA-pipelined kernel needs 16-byte aligned arrays and no body force (no state read)
         const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
         if (!kp.has_bf && kp.err != nullptr && al(Rin) && al(Rout) && al(dU) && al(U) && al(Uout)) {
@@ -1328,6 +1378,7 @@ void fill_launchers(Launchers& L) {
     L.features = Feat<N, QC, QV>::bits;
     L.op_fp64 = op_dispatch<double, N, QC, QV>;
     L.cb_fp64 = cells_per_cta<double, N, QC, QV>();
+    L.gws_fp64 = op_gws_bytes<double, N, QC, QV>();
   } else if constexpr (PART == 1) {  // FP32 operator (mixed form)
     L.op_fp32 = op_dispatch<float, N, QC, QV>;
     L.dev_fp32 = dev_launch<float, N>;

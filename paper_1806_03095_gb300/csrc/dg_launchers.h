@@ -56,16 +56,20 @@ struct Launchers {
   EkGradFn ekgrad;
   int (*dev_fp32)(const KParams&, const double* U, void* D, cudaStream_t);  // D = float(U - U_ref)
   int cb_fp64, cb_fp32;
+  // bytes per CTA of the global workspace of the CTA-wide operator kernels (0: everything in shared memory)
+  size_t gws_fp64;
   // per part: write the 1D tables (layout of make_layout, FP64 and FP32) to the part's constant memory on
   // the current device
   int (*const_tables[7])(const double* t64, const float* t32, cudaStream_t);
 };
 
 // (N = k+1, QC, QV) triples compiled into the library.  Default rules:
-// QC = floor(3k/2)+1 (3/2-rule, Sec. 2.2.3) and QV = k+1 (k = 1..7); plus the
+// QC = floor(3k/2)+1 (3/2-rule, Sec. 2.2.3) and QV = k+1 (k = 1..8, 11, 15); plus the
 // standard rule QC = QV = k+1 at k = 3, 5, the paper's own setting with the 3/2
 // rule on both terms (QV = QC) at k = 2..5, and the 2k+1 rule on both terms
-// (QC = QV = 2k+1) at k = 2..4 (Sec. 4.1.2, over-integration).
+// (QC = QV = 2k+1) at k = 2..5 and 7 (Sec. 4.1.2, over-integration).  From k = 8 (and
+// for the 2k+1 rule from k = 5) one cell's working set exceeds shared memory and the
+// CTA-wide operator kernels use the global workspace.
 #define DGCNS_CONFIGS(X) \
   X(2, 2, 2)             \
   X(3, 4, 3)             \
@@ -82,7 +86,12 @@ struct Launchers {
   X(6, 8, 8)             \
   X(3, 5, 5)             \
   X(4, 7, 7)             \
-  X(5, 9, 9)
+  X(5, 9, 9)             \
+  X(6, 11, 11)           \
+  X(8, 15, 15)           \
+  X(9, 13, 9)            \
+  X(12, 17, 12)          \
+  X(16, 23, 16)
 
 // Parts of each instantiation (separate translation units): FP64 operator, FP32 operator,
 // diagnostics + geometry, adjoint, FP64 face kernel, FP32 face kernel, adjoint face kernels.

@@ -271,6 +271,7 @@ struct dgcns_ctx {
   int* d_err = nullptr;  // error word of the kernels with bounded waits
   int* d_fnbr = nullptr;  // rotated-frame meshes: neighbour and orientation per local face
   int* d_flist = nullptr;  // rotated-frame meshes, face-centric kernels: faces by owner's local face
+  void* d_gws = nullptr;   // high degrees: global workspace of the operator kernels
   int diag_blocks = 0;
   int64_t launches = 0;
   // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
@@ -424,7 +425,9 @@ static std::vector<int> frame_face_table(const dgcns_mesh& m, const std::vector<
 
 // Face lists of the face-centric kernels on rotated-frame meshes: every face once, owned by the cell whose
 // local upper face it is (the lower-indexed cell when it is an upper or a lower face of both), grouped by the
-// owner's local face f = 2 d + s; off[f] and len[f] locate group f.
+// owner's local face f = 2 d + s, each group in owner order; off[f] and len[f] locate group f.  (Ordering the
+// groups by the box axis of the face, or interleaving the six groups block by block, did not reduce the
+// DRAM re-reads of the mixed form's face kernel, and the interleaving slowed the FP64 one: measured.)
 static std::vector<int> frame_face_lists(long long Nc, const std::vector<int>& t, int off[6], int len[6]) {
   std::vector<std::vector<int>> groups(6);
   for (long long e = 0; e < Nc; ++e)
@@ -569,7 +572,7 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
     return code;
   };
   const int k = prm->k;
-  if (k < 1 || k > 8) return bad(DGCNS_ERR_UNSUPPORTED, "k must be in 1..8");
+  if (k < 1 || k > 15) return bad(DGCNS_ERR_UNSUPPORTED, "k must be in 1..15");
   if (prm->nq_conv < k + 1 || prm->nq_visc < k + 1)
     return bad(DGCNS_ERR_INVALID_ARG, "nq_conv and nq_visc must be >= k+1 (collocation gradients)");
   for (int d = 0; d < 3; ++d) {
@@ -658,6 +661,17 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
   }
 
   if (cudaGetDevice(&c->device) != cudaSuccess) return create_fail(c, "cudaGetDevice");
+  if (prm->precision == DGCNS_FP64 && c->L.gws_fp64 > 0) {
+    // high degrees: the operator kernels' per-cell working set in a global workspace of 4 CTA slices per
+    // SM (the launcher runs the grid in chunks of that many CTAs)
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || nsm < 1)
+      return create_fail(c, "multiprocessor count");
+    const size_t ctas = (size_t)4 * nsm;
+    if (cudaMalloc(&c->d_gws, ctas * c->L.gws_fp64) != cudaSuccess) return create_fail(c, "operator workspace");
+    c->kp.gws = c->d_gws;
+    c->kp.gws_elems = ctas * c->L.gws_fp64 / sizeof(double);
+  }
   if (cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->d_tau, tau.size() * sizeof(double)) != cudaSuccess)
@@ -844,6 +858,7 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_err);
   cudaFree(c->d_fnbr);
   cudaFree(c->d_flist);
+  cudaFree(c->d_gws);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
     cudaFree(c->g32[i]);
@@ -987,10 +1002,10 @@ static int run_op(dgcns_ctx* c, int mode, KParams kp, const double* U, const voi
                   double* Uout) {
   const OpFn f = c->prm.precision == DGCNS_MIXED ? c->L.op_fp32 : c->L.op_fp64;
   TimedScope ts(c, op_kind(mode));
-  const int r = f(mode, kp, U, Rin, Rout, dU, Uout, c->stream);
-  c->launches += 1;
+  const int r = f(mode, kp, U, Rin, Rout, dU, Uout, c->stream);  // >= 0: launches made (0 stands for 1)
   if (r == -2) return fail(c, DGCNS_ERR_UNSUPPORTED, "operator variant not compiled or too large for shared memory");
-  if (r != 0) return cuda_fail(c, "operator kernel launch");
+  if (r < 0) return cuda_fail(c, "operator kernel launch");
+  c->launches += r > 0 ? r : 1;
   return DGCNS_OK;
 }
 

@@ -122,7 +122,7 @@ def _mesh_params(k, qc, qv, precision=0, kernel=2, mapping=0, geometry=0):
     (dict(k=2, qc=4, qv=3, mapping=2, geometry=1), -2),  # geometry on the fly only at k = 3
     (dict(k=3, qc=6, qv=4), -2),                         # no instantiation for this quadrature pair
     (dict(k=7, qc=11, qv=8, precision=1), -2),           # k = 7 only in FP64
-    (dict(k=5, qc=11, qv=11), -2),                       # the 2k+1 rule only up to k = 4
+    (dict(k=6, qc=13, qv=13), -2),                       # the 2k+1 rule at k = 2..5 and 7 only
     (dict(k=3, qc=5, qv=4, kernel=3), -1),               # unknown kernel organisation
     (dict(k=3, qc=5, qv=4, geometry=2), -1),             # unknown geometry mode
     (dict(k=3, qc=5, qv=4, precision=2), -1),            # unknown precision

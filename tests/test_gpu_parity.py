@@ -138,6 +138,48 @@ def test_over_integration_and_degree_seven(k, qc, qv):
     assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
+@pytest.mark.parametrize("k,qc,qv,ncells", [(8, 13, 9, (2, 3, 2)), (5, 11, 11, (2, 2, 2)), (7, 15, 15, (2, 1, 2)),
+                                            (11, 17, 12, (2, 2, 1)), (15, 23, 16, (2, 1, 1))])
+def test_high_degrees_global_workspace(k, qc, qv, ncells):
+    """Degrees whose cell working set exceeds shared memory (k = 8, 11, 15 with the default rule, the 2k+1 rule
+    at k = 5 and 7): the operator kernels keep it in the global workspace.  Face-centric kernels, FP64, F and
+    L against the oracle at 1e-12 on small periodic boxes (one or two cells along an axis); at k = 8 also an
+    RK stage."""
+    g, op = pair(ncells, k, qc, qv, kernel=2)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 40 + k)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    Lref = op.L(U)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), Lref)
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    if k == 8:
+        dU0 = inputs.uniform(U.shape, 41)
+        dt = 1e-3
+        dUg, Uo = on_gpu(dU0), g.empty_state()
+        g.rk_stage(3, dt, 0.0, on_gpu(U), dUg, Uo)
+        dU_ref = ork.A[3] * dU0 + dt * Lref
+        l2, mx = rel_err(dUg, dU_ref)
+        assert l2 < TOL64 and mx < TOL64, (l2, mx)
+        l2, mx = rel_err(Uo, U + ork.B[3] * dU_ref)
+        assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
+def test_high_degree_workspace_chunks():
+    """More cells than the global workspace holds (4 CTA slices per SM, so the operator kernel runs in
+    chunks): L at k = 8 on 9x9x9 cells, compared with the oracle's per-cell L on the cells at each chunk
+    boundary, the first and the last cell."""
+    g, op = pair((9, 9, 9), 8, 13, 9, kernel=2)
+    chunk = 4 * torch.cuda.get_device_properties(g.device).multi_processor_count
+    assert chunk < op.mesh.Nc
+    E = sorted({0, chunk - 1, chunk, 2 * chunk - 1, 2 * chunk, op.mesh.Nc - 1} & set(range(op.mesh.Nc)))
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 49)
+    n0 = g.dg_cns_launch_count()
+    out = g.apply(on_gpu(U), op=api.OP_L).cpu()
+    assert g.dg_cns_launch_count() - n0 == 1 + -(-op.mesh.Nc // chunk)  # the face kernel, then the chunks
+    l2, mx = rel_err(out[E], op.L_cells(U, E))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_single_cell_periodic_box(kernel):
     """Degenerate mesh: one cell per direction, the cell is its own neighbour on every face."""
