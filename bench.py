@@ -39,10 +39,14 @@ FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 # (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
 # The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
 TRAFFIC = {
-    ("faces", 0, 4, 5, 4): (15103.7, "908ebd0b7af2f3d6e49b1ac2b26c1030a17057255a1ae3b3c00640c63d7b56f0",
-                            "profiles/dg_face_kernel_fp64_tgv48_k3_full.md"),
-    ("cell_stage", 0, 4, 5, 4): (17680.0, "908ebd0b7af2f3d6e49b1ac2b26c1030a17057255a1ae3b3c00640c63d7b56f0",
-                                 "profiles/dg_op_kernel_cell_stage_fp64_tgv48_k3_full.md"),
+    ("faces", 0, 4, 5, 4): (15105.7, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+                            "profiles/face_centric_fp64_tgv64_k3_launches.md"),
+    ("cell_stage", 0, 4, 5, 4): (17652.8, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+                                 "profiles/face_centric_fp64_tgv64_k3_launches.md"),
+    ("faces", 1, 4, 5, 4): (7337.7, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+                            "profiles/dg_face_task_kernel_mixed_tgv48_k3.md"),
+    ("cell_stage", 1, 4, 5, 4): (13742.1, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+                                 "profiles/dg_cell_task_kernel_mixed_tgv48_k3.md"),
 }
 
 

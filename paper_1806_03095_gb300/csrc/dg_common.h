@@ -101,10 +101,6 @@ struct KParams {
   // that owns it; flist + foff[2 d + s] holds flen[2 d + s] owner cells (nullptr: structured enumeration).
   const int* flist;
   int foff[6], flen[6];
-  // Rotated-frame meshes, warp-per-face kernel: per cell the local faces 2 d + s that face the upper box side
-  // along x, y, z (4 bits each); the kernel then enumerates faces as on the aligned box, one box axis per
-  // grid row, and every cell owns its upper face.
-  const int* fbox;
   // Operator kernels whose per-cell working set does not fit shared memory (high degrees): a global
   // workspace of gws_elems values of the arithmetic type, one slice per CTA; the launcher runs the grid
   // in chunks of as many CTAs as it holds, the first cell of a chunk in cell0 (0 otherwise).

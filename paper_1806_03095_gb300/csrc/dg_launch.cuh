@@ -1217,16 +1217,10 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   const Tab<T> tb = load_tables<T, N, QC, QV>(static_cast<const T*>(kp.tables), stab);
   __syncthreads();
   const int w = threadIdx.x >> 5;
-  int d = blockIdx.y;
+  const int d = blockIdx.y;
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   int s, i;
-  if (kp.fbox) {  // rotated-frame meshes: cell i owns its upper face along box axis blockIdx.y
-    i = blockIdx.x * WPC + w;
-    if (i >= kp.Nc) return;  // only warp barriers below
-    const int f = (kp.fbox[i] >> (4 * blockIdx.y)) & 15;
-    d = f >> 1;
-    s = f & 1;
-  } else if (kp.flist) {  // the faces owned through local face (d, 1), then (d, 0)
+  if (kp.flist) {  // rotated-frame meshes: the faces owned through local face (d, 1), then (d, 0)
     const int nb1 = (kp.flen[2 * d + 1] + WPC - 1) / WPC;
     s = (int)blockIdx.x < nb1 ? 1 : 0;
     i = (s ? (int)blockIdx.x : (int)blockIdx.x - nb1) * WPC + w;
@@ -1256,8 +1250,8 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   int* en = eo + 1;
   int* oc = eo + 2;  // rotated-frame meshes: orientation code of the other cell
   const PhysT<T> ph = make_phys<T>(kp);
-  if (grp.rank() == 0 && (kp.fbox || kp.flist)) {
-    const int e = kp.fbox ? i : kp.flist[kp.foff[2 * d + s] + i];
+  if (grp.rank() == 0 && kp.flist) {
+    const int e = kp.flist[kp.foff[2 * d + s] + i];
     const int* t = kp.fnbr + ((size_t)e * 6 + 2 * d + s) * 2;
     eo[0] = e;
     en[0] = t[0];
@@ -1291,7 +1285,7 @@ __global__ void __launch_bounds__(WPC * 32) dg_face_warp_kernel(const KParams kp
   }
   grp.sync();
   const T* Ud = static_cast<const T*>(kp.Udev);
-  const int* ocp = kp.fbox || kp.flist ? oc : nullptr;
+  const int* ocp = kp.flist ? oc : nullptr;
   if (GEO == GEO_FLY) {
     const T* X = static_cast<const T*>(kp.xyzT);
     for (int r = grp.rank(); r < 3 * N3; r += 32) {
@@ -1341,8 +1335,7 @@ int launch_faces(const KParams& kp, const double* U, void* FB, cudaStream_t st) 
     auto k = dg_face_warp_kernel<T, N, QC, QV, WPC, GEO>;
     static bool attr[kMaxDevices] = {};
     if (smem_attr_once(k, smem, attr)) return -1;
-    const dim3 grid(kp.flist && !kp.fbox ? list_blocks(WPC)
-                                         : (kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
+    const dim3 grid(kp.flist ? list_blocks(WPC) : (kp.Nc + WPC - 1) / WPC + (extra_items + WPC - 1) / WPC, 3);
     k<<<grid, WPC * 32, smem, st>>>(kp, U, static_cast<T*>(FB));
   } else {
     constexpr int CB = faces_per_cta<T, N, QC, QV, GEO>();

@@ -272,7 +272,6 @@ struct dgcns_ctx {
   int* d_fnbr = nullptr;  // rotated-frame meshes: neighbour and orientation per local face
   int* d_flist = nullptr;  // rotated-frame meshes, face-centric kernels: faces by owner's local face
   void* d_gws = nullptr;   // high degrees: global workspace of the operator kernels
-  int* d_fbox = nullptr;   // rotated-frame meshes, warp-per-face kernel: local faces facing +x, +y, +z
   int diag_blocks = 0;
   int64_t launches = 0;
   // per-kernel timing (dg_cns_timing): event pairs awaiting readout, a pool of free events, totals
@@ -811,16 +810,6 @@ int dg_cns_create(const dgcns_mesh* mesh, const dgcns_params* prm, void* stream,
       if (cudaMemcpy(c->d_flist, fl.data(), fl.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return create_fail(c, "face list upload");
       kp.flist = c->d_flist;
-      // the local face of each cell facing the upper box side along each axis
-      const std::vector<int> frames = cell_frames(*mesh);
-      std::vector<int> fb((size_t)c->Nc, 0);
-      for (long long e = 0; e < c->Nc; ++e)
-        for (int a = 0; a < 3; ++a)
-          fb[(size_t)e] |= (2 * frame_axis(frames[(size_t)e], a) + (frame_flip(frames[(size_t)e], a) ? 0 : 1)) << (4 * a);
-      if (cudaMalloc(&c->d_fbox, fb.size() * sizeof(int)) != cudaSuccess) return create_fail(c, "box faces");
-      if (cudaMemcpy(c->d_fbox, fb.data(), fb.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-        return create_fail(c, "box face upload");
-      kp.fbox = c->d_fbox;
     }
   }
   // diagnostics partial sums
@@ -870,7 +859,6 @@ int dg_cns_destroy(dgcns_ctx* c) {
   cudaFree(c->d_fnbr);
   cudaFree(c->d_flist);
   cudaFree(c->d_gws);
-  cudaFree(c->d_fbox);
   for (int i = 0; i < 5; ++i) {
     cudaFree(c->g64[i]);
     cudaFree(c->g32[i]);

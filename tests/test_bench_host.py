@@ -37,7 +37,7 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     monkeypatch.setattr(bench, "kernel_digest", lambda: "another")
     t, src = bench.traffic_per_launch("faces", 0, 4, 5, 4, 10)
     assert t is None and "changed" in src
-    assert bench.traffic_per_launch("faces", 1, 4, 5, 4, 10) == (None, None)
+    assert bench.traffic_per_launch("faces", 1, 9, 13, 9, 10) == (None, None)  # never captured
 
 
 @pytest.mark.parametrize("N,QC,QV", [(3, 4, 3), (4, 5, 4), (6, 8, 6)])
