@@ -94,15 +94,25 @@ def kernel_flops(kind, N, QC, QV, Nc):
 
 
 def kernel_bytes(kind, N, Nc, rbytes):
-    """Algorithmic HBM bytes of one launch (stages 1..4: dU read): U in FP64, residual-type dU and face shares."""
+    """Algorithmic HBM bytes of one launch (stages 1..4: dU read), as the kernels run inside dg_cns_rk_steps.
+
+    FP64 (rbytes 8): the operator kernels read U (8 B per value).  Mixed form (rbytes 4): they read the FP32
+    deviation state (4 B per value), and the stage kernels of the fused and face-centric organisations also
+    read U for the FP64 update and write the next deviation state.  Every stage kernel reads U, reads and
+    writes dU and writes U_out; the split M^-1 + stage kernel also reads the residual.  Face shares: 60 n^2
+    values per cell."""
     nodes = Nc * N ** 3
+    v = nodes * 5
     shares = 60 * N * N * Nc * rbytes
-    per = {"fused": nodes * stage_bytes_per_node(rbytes),
-           "faces": nodes * 5 * 8 + shares,
-           "cell_stage": nodes * stage_bytes_per_node(rbytes) + shares,
-           "cell": nodes * 5 * (8 + rbytes),
-           "face": nodes * 5 * (8 + 2 * rbytes),
-           "mass": nodes * stage_bytes_per_node(rbytes) - nodes * 5 * 8 + nodes * 5 * rbytes}
+    s = 8 if rbytes == 8 else 4
+    dev = 0 if rbytes == 8 else 4 + 4
+    upd = v * (8 + rbytes + rbytes + 8)
+    per = {"fused": upd + v * dev,
+           "faces": v * s + shares,
+           "cell_stage": upd + v * dev + shares,
+           "cell": v * (s + rbytes),
+           "face": v * (s + 2 * rbytes),
+           "mass": upd + v * rbytes}
     return per.get(kind)
 
 

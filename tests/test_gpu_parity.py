@@ -164,6 +164,18 @@ def test_high_degrees_global_workspace(k, qc, qv, ncells):
         assert l2 < TOL64 and mx < TOL64, (l2, mx)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("k,qc,qv,ncells", [(8, 13, 9, (2, 2, 3)), (11, 17, 12, (2, 1, 1))])
+def test_high_degrees_element_centric(k, qc, qv, ncells, kernel):
+    """The split and fused (element-centric) kernels from the global workspace: F and L at 1e-12."""
+    g, op = pair(ncells, k, qc, qv, kernel=kernel)
+    U = inputs.random_state(op.mesh.Nc, op.mesh.n ** 3, 60 + k)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_F), op.residual(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+    l2, mx = rel_err(g.apply(on_gpu(U), op=api.OP_L), op.L(U))
+    assert l2 < TOL64 and mx < TOL64, (l2, mx)
+
+
 def test_high_degree_workspace_chunks():
     """More cells than the global workspace holds (4 CTA slices per SM, so the operator kernel runs in
     chunks): L at k = 8 on 9x9x9 cells, compared with the oracle's per-cell L on the cells at each chunk
