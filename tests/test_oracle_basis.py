@@ -73,3 +73,42 @@ def test_point_sets():
     fp, fw = face_points(3, 1, 1)
     assert np.allclose(fp[:, 1], 1.0) and abs(fw.sum() - 1) < 1e-15
     assert np.allclose(fp[1], [x[1], 1.0, x[0]]) and np.allclose(fp[3], [x[0], 1.0, x[1]])
+
+
+@pytest.mark.parametrize("nq", [13, 15, 16, 17, 23])
+def test_gauss_exact_high_point_counts(nq):
+    """The point counts of the high-degree rules (q = 13, 17, 23 of k = 8, 11, 15; 15 of the 2k+1 rule at
+    k = 7): exact to degree 2 nq - 1, relative to each moment; symmetric about 1/2; weights sum to 1."""
+    x, w = gauss_legendre_01(nq)
+    assert np.all(np.diff(x) > 0) and np.all(w > 0)
+    assert np.allclose(x + x[::-1], 1.0, atol=1e-15, rtol=0) and np.allclose(w, w[::-1], atol=1e-15, rtol=0)
+    for j in range(2 * nq):
+        assert abs((w * x ** j).sum() * (j + 1) - 1.0) < 1e-13, j
+
+
+@pytest.mark.parametrize("k", [11, 15])
+def test_lgl_nodes_high_degree(k):
+    x = lgl_nodes_01(k)
+    assert len(x) == k + 1 and x[0] == 0.0 and x[-1] == 1.0 and np.all(np.diff(x) > 0)
+    assert np.allclose(x + x[::-1], 1.0, atol=1e-15, rtol=0)
+    t = 2 * x - 1
+    # interior nodes are the roots of P_k'
+    assert np.abs(np.polynomial.legendre.Legendre.basis(k).deriv()(t[1:-1])).max() < 1e-9
+    w = 1.0 / (k * (k + 1) * np.polynomial.legendre.Legendre.basis(k)(t) ** 2)
+    for j in range(2 * k):
+        assert abs((w * x ** j).sum() * (j + 1) - 1.0) < 1e-12, j
+
+
+@pytest.mark.parametrize("k", [11, 15])
+def test_lagrange_properties_high_degree(k):
+    nodes = lgl_nodes_01(k)
+    V, D = lagrange_1d(nodes, nodes)
+    assert np.allclose(V, np.eye(k + 1), atol=1e-13)
+    xs = np.linspace(0.0, 1.0, 41)
+    V, D = lagrange_1d(nodes, xs)
+    assert np.allclose(V.sum(1), 1.0, atol=1e-12)
+    assert np.abs(D.sum(1)).max() < 1e-8
+    rng = np.random.default_rng(k)
+    p = np.polynomial.Legendre(rng.standard_normal(k + 1), domain=[0, 1])
+    assert np.allclose(V @ p(nodes), p(xs), atol=1e-11)
+    assert np.allclose(D @ p(nodes), p.deriv()(xs), atol=1e-7 * np.abs(p.deriv()(xs)).max())

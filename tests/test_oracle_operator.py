@@ -152,6 +152,18 @@ def test_discrete_conservation_periodic(mapping, A):
     assert torch.all(tot.abs() <= 1e-13 * scale)
 
 
+@pytest.mark.parametrize("k,A", [(8, 0.0), (8, 0.05), (11, 0.0)])
+def test_free_stream_and_conservation_high_degree(k, A):
+    """The degrees of the global-workspace kernels (default rule q_c = floor(3k/2)+1, q_v = k+1): free-stream
+    preservation and discrete conservation of a random state on 2^3 periodic cells, affine and deformed."""
+    mesh = tgv_mesh(2, k, MAP_SINE if A else MAP_AFFINE, A)
+    op = make_op(mesh)
+    R = op.residual(const_state(mesh.Nc, mesh.n ** 3))
+    assert float(R.abs().max()) < 5e-11
+    R = op.residual(inputs.random_state(mesh.Nc, mesh.n ** 3, 12))
+    assert torch.all(R.sum((0, 2)).abs() <= 1e-12 * R.abs().sum((0, 2)))
+
+
 def test_channel_wall_conserves_mass():
     mesh = BoxMesh((2, 2, 2), [0, -1, 0], [2 * PI, 1, PI], (1, 0, 1), 3, MAP_CHANNEL, 1.8)
     phys = ph.Physics.from_numbers(180.0, 0.71, 0.1, u_mach=18.3, body_force=(1.0, 0.0, 0.0))
