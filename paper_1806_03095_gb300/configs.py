@@ -37,6 +37,8 @@ WORKLOADS = {
     "tgv32_k3": lambda **kw: tgv(32, 3, **kw),
     "tgv40_k5": lambda **kw: tgv(40, 5, **kw),
     "tgv24_k4": lambda **kw: tgv(24, 4, **kw),
+    "tgv16_k15": lambda **kw: tgv(16, 15, **kw),
+    "tgv8_k15": lambda **kw: tgv(8, 15, **kw),
     "channel32_k3": lambda **kw: channel(32, 3, **kw),
 }
 
