@@ -128,7 +128,11 @@ typedef struct {
  * makes the context's device current for the call and restores the caller's
  * current device before it returns.  `stream` is a cudaStream_t of that
  * device (NULL = legacy default stream).  Builds the host plan (1D tables in FP64,
- * penalty per cell, geometry) and allocates the context's device buffers.
+ * penalty per cell, geometry) and allocates the context's device buffers.  Where one
+ * cell's working set exceeds a CTA's shared memory (FP64 from k = 8, and the 2k+1 rule
+ * from k = 5), it also allocates a workspace of four cell slices per SM (about 0.2 GB
+ * at k = 8 and 1.1 GB at k = 15 on 152 SMs); the operator kernels then run in chunks
+ * of that many cells.  Rotated-frame meshes add a face table of 12 ints per cell.
  * Errors: INVALID_ARG (sizes: every n[d] >= 1 and at most 2^30 cells in all;
  * physics), UNSUPPORTED (no instantiation for (k, nq_conv, nq_visc)), OOM,
  * CUDA.  *out is NULL on error. */
