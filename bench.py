@@ -39,13 +39,13 @@ FP32_PEAK_TFLOPS = 73.5  # measured FP32 FMA throughput, same probe
 # (kind, precision 0/1, N, QC, QV) -> (bytes per cell, sources digest, profile summary under profiles/).
 # The roofline reports traffic = bytes per cell x cells only while the sources still have that digest.
 TRAFFIC = {
-    ("faces", 0, 4, 5, 4): (15105.7, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+    ("faces", 0, 4, 5, 4): (15115.6, "cc826ba75499d748a67d4103685ebe4090f2818998df31d1db553338e0ad948a",
                             "profiles/face_centric_fp64_tgv64_k3_launches.md"),
-    ("cell_stage", 0, 4, 5, 4): (17652.8, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+    ("cell_stage", 0, 4, 5, 4): (17651.0, "cc826ba75499d748a67d4103685ebe4090f2818998df31d1db553338e0ad948a",
                                  "profiles/face_centric_fp64_tgv64_k3_launches.md"),
-    ("faces", 1, 4, 5, 4): (7337.7, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+    ("faces", 1, 4, 5, 4): (7333.7, "cc826ba75499d748a67d4103685ebe4090f2818998df31d1db553338e0ad948a",
                             "profiles/dg_face_task_kernel_mixed_tgv48_k3.md"),
-    ("cell_stage", 1, 4, 5, 4): (13742.1, "6f1bcad212d9ef30d578c63ffd738d181d26a113128f37b04a48cb2af90c1641",
+    ("cell_stage", 1, 4, 5, 4): (13743.6, "cc826ba75499d748a67d4103685ebe4090f2818998df31d1db553338e0ad948a",
                                  "profiles/dg_cell_task_kernel_mixed_tgv48_k3.md"),
 }
 

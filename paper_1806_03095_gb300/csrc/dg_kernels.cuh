@@ -213,15 +213,20 @@ __device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ 
     T y[DOUT];
 #pragma unroll
     for (int q = 0; q < OH; ++q) {
-      T e = (DIN & 1) ? C[q] * xm : T(0);
+      // the centre output of an odd-length result: a symmetric operator (SYM > 0) has no odd part there and an
+      // antisymmetric one no even part (exactly, for the symmetric point sets; the tables hold rounding-level
+      // values), so only the other half is formed
+      const bool centre = (DOUT & 1) && q == OH - 1;
+      const bool need_e = !(centre && SYM < 0), need_o = !(centre && SYM > 0);
+      T e = (DIN & 1) && need_e ? C[q] * xm : T(0);
       T o = T(0);
 #pragma unroll
       for (int i = 0; i < IH; ++i) {
-        e += A[q * IH + i] * xe[i];
-        o += B[q * IH + i] * xo[i];
+        if (need_e) e += A[q * IH + i] * xe[i];
+        if (need_o) o += B[q * IH + i] * xo[i];
       }
-      if ((DOUT & 1) && q == OH - 1) {
-        y[q] = e + o;
+      if (centre) {
+        y[q] = SYM > 0 ? e : o;
       } else {
         y[q] = e + o;
         y[DOUT - 1 - q] = SYM > 0 ? e - o : o - e;
