@@ -300,6 +300,16 @@ int dg_cns_timing(dgcns_ctx* ctx, int enable);
    enabled.  Either pointer may be NULL. */
 int dg_cns_kernel_times(dgcns_ctx* ctx, double* ms, int64_t* counts, int n);
 
+/* Host only (no device, no context): the reference frames and the face table that dg_cns_create
+ * builds for a DGCNS_MAP_ROTATED mesh.  frames[e] (n cells ints): the frame g of cell e.
+ * table[(e 6 + 2 d + s) 2] (12 n cells ints): the neighbour across local face (d, s) of cell e;
+ * table[(e 6 + 2 d + s) 2 + 1]: its orientation code.  Seen in e's frame and moved across that face,
+ * the neighbour's node (i0, i1, i2) is its own node (j0, j1, j2) with j_b = i_a, or N-1-i_a when bit
+ * 6 + b of the code is set, where a is held in bits 2b..2b+1.  Either output may be NULL (not both);
+ * both are caller-owned.  Errors: INVALID_ARG (not a rotated-frame mesh, a non-periodic axis, bad
+ * extents, seed or cell count; message through dg_cns_last_error(NULL)).  (Library utility.) */
+int dg_cns_face_table(const dgcns_mesh* mesh, int* table, int* frames);
+
 /* Message of the last error on this context (static string if ctx is NULL; the message of a failed
  * dg_cns_create when ctx is NULL).  (Library utility, no counterpart in the paper.) */
 const char* dg_cns_last_error(const dgcns_ctx* ctx);

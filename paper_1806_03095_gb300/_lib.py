@@ -28,7 +28,7 @@ EXPORTS = ("dg_cns_create", "dg_cns_destroy", "dg_cns_set_stream", "dg_cns_sizes
            "dg_cns_lsrk_steps", "dg_cns_diagnostics",
            "dg_cns_diagnostics_noalloc", "dg_cns_adjoint_apply", "dg_cns_rk_stage_adjoint",
            "dg_cns_kinetic_energy_gradient", "dg_cns_launch_count", "dg_cns_status", "dg_cns_timing", "dg_cns_kernel_times",
-           "dg_cns_last_error")
+           "dg_cns_face_table", "dg_cns_last_error")
 
 # Kernel kinds of dg_cns_kernel_times (DGCNS_KT_*).
 KERNEL_KINDS = ("cell", "face", "mass", "fused", "faces", "cell_stage", "dev", "adj_prep", "adj_faces", "adj",
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "dg_cns_status": ([vp], ci),
         "dg_cns_timing": ([vp, ci], ci),
         "dg_cns_kernel_times": ([vp, dp, i64p, ci], ci),
+        "dg_cns_face_table": ([ctypes.POINTER(Mesh), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ci),
         "dg_cns_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():

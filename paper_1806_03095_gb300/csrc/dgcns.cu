@@ -3,6 +3,7 @@
 // instantiations, and the C ABI of include/dgcns.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1449,6 +1450,32 @@ int dg_cns_kernel_times(dgcns_ctx* c, double* ms, int64_t* counts, int n) {
   for (int i = 0; i < n; ++i) {
     if (ms) ms[i] = c->kt_ms[i];
     if (counts) counts[i] = c->kt_n[i];
+  }
+  return DGCNS_OK;
+}
+
+int dg_cns_face_table(const dgcns_mesh* mesh, int* table, int* frames) {
+  auto bad = [](const char* m) {
+    g_create_err = m;
+    return DGCNS_ERR_INVALID_ARG;
+  };
+  if (!mesh || (!table && !frames)) return bad("null mesh, or neither output given");
+  if (mesh->mapping != DGCNS_MAP_ROTATED) return bad("the mesh is not a rotated-frame mesh");
+  long long ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh->n[d] < 1 || !(mesh->hi[d] > mesh->lo[d])) return bad("bad mesh extents");
+    if (!mesh->periodic[d]) return bad("rotated-frame meshes must be periodic on every axis");
+    ncell *= mesh->n[d];
+    if (ncell > (1LL << 30)) return bad("too many cells (more than 2^30)");
+  }
+  if (!(mesh->map_param >= 0.0 && mesh->map_param < 18446744073709551616.0) ||
+      mesh->map_param != std::floor(mesh->map_param))
+    return bad("the frame seed (map_param) must be a non-negative integer below 2^64");
+  const std::vector<int> fr = cell_frames(*mesh);
+  if (frames) std::copy(fr.begin(), fr.end(), frames);
+  if (table) {
+    const std::vector<int> t = frame_face_table(*mesh, fr);
+    std::copy(t.begin(), t.end(), table);
   }
   return DGCNS_OK;
 }
