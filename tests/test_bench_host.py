@@ -59,3 +59,18 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+
+
+def test_algorithmic_bytes_per_kernel_kind():
+    """Per cell at k = 3 (320 values): the byte counts the roofline uses are the blocks each kernel moves.
+    FP64: face kernel U + shares (2,560 + 7,680), cell + stage U, dU read and written, U_out, shares
+    (4 x 2,560 + 7,680), split M^-1 + stage R, dU read and written, U, U_out (5 x 2,560).  Mixed form:
+    the operator kernels read the FP32 deviation state and the stage kernels write the next one."""
+    kb = lambda kind, rb: roofline.kernel_bytes(kind, 4, 1, rb)
+    assert kb("faces", 8) == 2560 + 7680
+    assert kb("cell_stage", 8) == 4 * 2560 + 7680
+    assert kb("mass", 8) == 5 * 2560
+    assert kb("fused", 8) == 4 * 2560
+    assert kb("faces", 4) == 1280 + 3840
+    assert kb("cell_stage", 4) == 2560 + 1280 + 2 * 1280 + 2560 + 1280 + 3840
+    assert kb("mass", 4) == 1280 + 2 * 1280 + 2560 + 2560
