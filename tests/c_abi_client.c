@@ -73,6 +73,28 @@ int main(int argc, char** argv) {
   p.nq_visc = 9;
   expect("create_not_instantiated", dg_cns_create(&m, &p, NULL, &ctx), DGCNS_ERR_UNSUPPORTED);
 
+  /* host-only face table of a rotated-frame mesh: neighbours are cell indices, frames lie in [0, 48),
+     orientation codes in 9 bits; a wall is refused */
+  {
+    dgcns_mesh r;
+    int table[8 * 12], frames[8];
+    memset(&r, 0, sizeof r);
+    for (int d = 0; d < 3; ++d) {
+      r.n[d] = 2;
+      r.hi[d] = 1.0;
+      r.periodic[d] = 1;
+    }
+    r.mapping = DGCNS_MAP_ROTATED;
+    r.map_param = 1806.0;
+    expect("face_table", dg_cns_face_table(&r, table, frames), DGCNS_OK);
+    for (int i = 0; i < 8; ++i)
+      if (frames[i] < 0 || frames[i] > 47) ++failures;
+    for (int i = 0; i < 8 * 6; ++i)
+      if (table[2 * i] < 0 || table[2 * i] > 7 || table[2 * i + 1] < 0 || table[2 * i + 1] > 511) ++failures;
+    r.periodic[2] = 0;
+    expect("face_table_wall", dg_cns_face_table(&r, table, frames), DGCNS_ERR_INVALID_ARG);
+  }
+
   expect("create_null_out", dg_cns_create(&m, &p, NULL, NULL), DGCNS_ERR_INVALID_ARG);
   expect("destroy_null", dg_cns_destroy(NULL), DGCNS_ERR_INVALID_ARG);
   expect("apply_null", dg_cns_apply(NULL, NULL, NULL, DGCNS_OP_L), DGCNS_ERR_INVALID_ARG);
