@@ -531,7 +531,8 @@ def test_rotated_frames_cover_reflections_and_cycles():
     assert len(set((mr.frames // 8).tolist())) >= 4 and mr.flip.any(0).all()
 
 
-@pytest.mark.parametrize("k,qc,qv,deform", [(3, 5, 4, 0.0), (2, 3, 3, 0.0), (3, 5, 4, 0.05), (2, 4, 3, 0.08)])
+@pytest.mark.parametrize("k,qc,qv,deform", [(3, 5, 4, 0.0), (2, 3, 3, 0.0), (3, 5, 4, 0.05), (2, 4, 3, 0.08),
+                                           (1, 2, 2, 0.0), (4, 7, 5, 0.04)])
 def test_rotated_frame_operator_invariance(k, qc, qv, deform):
     assert _rotated_invariance_gap(k=k, qc=qc, qv=qv, deform=deform) < 1e-12
 
